@@ -1,0 +1,184 @@
+"""Seeded synthetic inputs shaped like the paper's experiments (arXiv:1804.01184).
+
+This module is shared by the tests, the oracle checks and the benchmark.  It generates
+inputs only -- contrast fields, acquisition geometry, the source wavelet, observed-data
+stand-ins -- and holds none of the method's arithmetic (no parameter maps, stencils,
+propagation or gradients).  Every array is returned in the precision the CUDA library
+consumes (float32); the oracle receives the same values widened to float64, so both sides
+see bit-identical inputs.
+
+Workloads (the paper measures on no public dataset; these stand in for its synthetic
+experiments, Sec. "Almost Well-posed Example" and the scatterer table):
+
+  * ``config_point`` -- 201 x 201 nodes, dx 5 m, 4th order, dt 0.5 ms, 800 steps, 15 Hz
+    Ricker, 8 sources / 64 receivers on a 400 m circle around the centre, 40-cell sponge
+    outside the stated grid, point scatterer with +10 % K and +10 % rho (K-rho contrasts).
+  * ``config_gaussian`` -- 601 x 601, dx 5 m, 8th order, 3000 steps, 64 sources / 256
+    receivers on a 1200 m circle, Gaussian scatterer (sigma 20 m) in vp or rho only, contrast
+    amplitude in [-0.5, 0.5] (vp-rho contrasts).
+  * ``config_paper`` -- the paper's own acquisition: 10 sources, 100 receivers, 490 m
+    circle, 5 Hz Ricker, vp = 2000 m/s, rho = 2000 kg/m^3, Gaussian sigma 50 m.
+  * ``small_case`` -- seeded random heterogeneous models on small grids for parity tests.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+PZ_VP_RHO, PZ_IP_RHO, PZ_VP_IP, PZ_K_RHO, PZ_INVK_INVRHO = range(5)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    nz: int
+    dx: float
+    dt: float
+    nt: int
+    order: int
+    sponge: int
+    vp_o: float
+    rho_o: float
+    pz: int                 # parameterization of xi_a / xi_b
+    xi_a: np.ndarray        # [nz][nx] float32 contrasts of the true model
+    xi_b: np.ndarray
+    src_xy: np.ndarray      # [ns][2] float32 metres, physical origin at node (0, 0)
+    rec_xy: np.ndarray      # [nr][2] float32
+    wavelet: np.ndarray     # [nt] float32, sample n at time (n + 1/2) dt
+    sponge_v: float = 0.0   # 0 -> vp_o
+    sponge_R: float = 1e-3
+
+    @property
+    def ns(self):
+        return self.src_xy.shape[0]
+
+    @property
+    def nr(self):
+        return self.rec_xy.shape[0]
+
+    @property
+    def Nx(self):
+        return self.nx + 2 * self.sponge
+
+    @property
+    def Nz(self):
+        return self.nz + 2 * self.sponge
+
+    def cell_updates(self, shots=None):
+        """Computational cells (sponge included) x steps x shots for one forward pass."""
+        return self.Nx * self.Nz * self.nt * (self.ns if shots is None else shots)
+
+    def background(self):
+        z = np.zeros((self.nz, self.nx), np.float32)
+        return z, z.copy()
+
+    def grid_kwargs(self):
+        return dict(nx=self.nx, nz=self.nz, dx=self.dx, dt=self.dt, nt=self.nt, order=self.order,
+                    sponge=self.sponge, vp_o=self.vp_o, rho_o=self.rho_o,
+                    sponge_v=self.sponge_v or self.vp_o, sponge_R=self.sponge_R)
+
+    def subset(self, shots):
+        """The same workload restricted to the listed shots."""
+        w = dataclasses.replace(self)
+        w.src_xy = np.ascontiguousarray(self.src_xy[list(shots)])
+        return w
+
+
+def ricker(nt, dt, f_peak, t0=None):
+    """Ricker wavelet (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2), tau = t - t0, t0 = 1/f,
+    amplitude 1, sampled at t = (n + 1/2) dt (the time of the n-th source increment)."""
+    t0 = 1.0 / f_peak if t0 is None else t0
+    t = (np.arange(nt, dtype=np.float64) + 0.5) * dt - t0
+    a = (math.pi * f_peak * t) ** 2
+    return ((1.0 - 2.0 * a) * np.exp(-a)).astype(np.float32)
+
+
+def circle(n, radius, centre, phase=0.0):
+    """n points evenly on a circle, angles 2 pi (k + phase) / n, as float32 [n][2] (x, z)."""
+    th = 2.0 * math.pi * (np.arange(n) + phase) / n
+    xy = np.stack([centre[0] + radius * np.cos(th), centre[1] + radius * np.sin(th)], axis=1)
+    return xy.astype(np.float32)
+
+
+def gaussian(nx, nz, dx, centre, sigma):
+    """exp(-|x - x0|^2 / (2 sigma^2)) on the physical nodes, float32 [nz][nx]."""
+    x = np.arange(nx) * dx - centre[0]
+    z = np.arange(nz) * dx - centre[1]
+    r2 = x[None, :] ** 2 + z[:, None] ** 2
+    return np.exp(-r2 / (2.0 * sigma * sigma)).astype(np.float32)
+
+
+def point(nx, nz):
+    """One at the centre node, zero elsewhere, float32 [nz][nx]."""
+    f = np.zeros((nz, nx), np.float32)
+    f[nz // 2, nx // 2] = 1.0
+    return f
+
+
+def centre_of(nx, nz, dx):
+    return ((nx - 1) * dx / 2.0, (nz - 1) * dx / 2.0)
+
+
+def config_point(nt=800):
+    nx = nz = 201
+    dx = 5.0
+    c = centre_of(nx, nz, dx)
+    f = point(nx, nz) * np.float32(0.1)
+    return Workload("point-201x201-o4", nx, nz, dx, 5e-4, nt, 4, 40, 2000.0, 2000.0, PZ_K_RHO,
+                    f.copy(), f.copy(), circle(8, 400.0, c), circle(64, 400.0, c, 0.5),
+                    ricker(nt, 5e-4, 15.0))
+
+
+def config_gaussian(amplitude=0.3, which="vp", nt=3000, ns=64, nr=256, n=601):
+    dx = 5.0
+    c = centre_of(n, n, dx)
+    g = gaussian(n, n, dx, c, 20.0) * np.float32(amplitude)
+    z = np.zeros_like(g)
+    xa, xb = (g, z) if which == "vp" else (z, g)
+    radius = 1200.0 * (n - 1) / 600.0
+    return Workload(f"gaussian-{n}x{n}-o8", n, n, dx, 5e-4, nt, 8, 40, 2000.0, 2000.0, PZ_VP_RHO,
+                    xa, xb, circle(ns, radius, c), circle(nr, radius, c, 0.5),
+                    ricker(nt, 5e-4, 15.0))
+
+
+def config_paper(nt=1400, which="vp", amplitude=0.2):
+    """The paper's acquisition: 10 sources, 100 receivers on a 490 m circle, 5 Hz, sigma 50 m."""
+    dx = 10.0
+    n = 121
+    c = centre_of(n, n, dx)
+    g = gaussian(n, n, dx, c, 50.0) * np.float32(amplitude)
+    z = np.zeros_like(g)
+    xa, xb = (g, z) if which == "vp" else (z, g)
+    return Workload("paper-121x121-o8", n, n, dx, 1e-3, nt, 8, 40, 2000.0, 2000.0, PZ_VP_RHO,
+                    xa, xb, circle(10, 490.0, c), circle(100, 490.0, c, 0.5),
+                    ricker(nt, 1e-3, 5.0))
+
+
+def small_case(seed=0, nx=45, nz=37, nt=120, order=8, sponge=6, ns=3, nr=7, pz=PZ_VP_RHO,
+               amp=0.15, dx=5.0, dt=5e-4, f_peak=25.0):
+    """Seeded heterogeneous model on a small grid: smooth random contrasts of size ~amp,
+    sources and receivers at random positions inside the physical grid."""
+    rng = np.random.default_rng(seed)
+
+    def smooth():
+        f = rng.standard_normal((nz, nx))
+        for _ in range(3):   # a few passes of a 3-point box filter
+            f = (np.roll(f, 1, 0) + f + np.roll(f, -1, 0)) / 3.0
+            f = (np.roll(f, 1, 1) + f + np.roll(f, -1, 1)) / 3.0
+        f /= max(1e-12, np.abs(f).max())
+        return (amp * f).astype(np.float32)
+
+    lo = np.array([2.0 * dx, 2.0 * dx])
+    hi = np.array([(nx - 3) * dx, (nz - 3) * dx])
+    src = (lo + (hi - lo) * rng.random((ns, 2))).astype(np.float32)
+    rec = (lo + (hi - lo) * rng.random((nr, 2))).astype(np.float32)
+    return Workload(f"small-{nx}x{nz}-o{order}-s{seed}", nx, nz, dx, dt, nt, order, sponge,
+                    2000.0, 2000.0, pz, smooth(), smooth(), src, rec, ricker(nt, dt, f_peak))
+
+
+def random_like(shape, seed, scale=1.0):
+    """Seeded standard-normal float32 array (perturbations, residuals, test vectors)."""
+    return (np.random.default_rng(seed).standard_normal(shape) * scale).astype(np.float32)
