@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the Scheme III hot path (arXiv:1804.01184) on GB300.
+
+One step = one pass of the whole hot path over one batch of the Gaussian-scatterer workload
+(601 x 601 physical nodes + 40-cell sponge = 681 x 681, dx 5 m, 8th order, dt 0.5 ms, 3000
+steps, 64 sources / 256 receivers on a 1200 m circle, Gaussian sigma 20 m, contrast swept
+over [-0.5, 0.5] in vp and in rho, one value per step):
+  1. fwi_model    : observed data of the true model                     (model build, forward)
+  2. fwi_gradient : misfit and gradient at the background for all five   (forward + snapshots,
+                    parameterizations                                      residual, adjoint, chain rule)
+  3. fwi_born     : Born traces of the true contrast around the background
+Metric: algorithmic cell-updates per second (computational cells incl. sponge x steps x
+shots x propagation passes: model 1, gradient 2 (forward + adjoint), Born 1; recomputed
+forward steps are not counted) and FWI gradients per second.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; every rank solves its own problems (different
+contrasts), so there is no collective on the data path ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s & FWI gradients/s vs plain per-shot GPU; p50/p99 solve latency"
+UNIT = "Gcell-updates/s"
+
+# Algorithmic HBM bytes per computational cell and shot for one launch of each stencil kernel
+# (FP32 fields: reads + writes each field once); model arrays shared by the shots of a
+# launch are counted once per launch (MODEL_BYTES per cell).
+KERNEL_BYTES = {
+    "k_fwd_v": 20, "k_fwd_p<false>": 16, "k_fwd_p<true>": 20,
+    "k_adj_v": 52, "k_adj_p": 16,
+    "k_born_v": 40, "k_born_p": 32,
+}
+MODEL_BYTES = {"k_fwd_v": 8, "k_fwd_p": 4, "k_adj_v": 4, "k_adj_p": 8, "k_born_v": 16, "k_born_p": 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nt", type=int, default=3000)
+    ap.add_argument("--shots", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def contrast_of(k, rank):
+    """Step k of rank r: amplitude from the sweep {-0.5, ..., 0.5} \\ {0}, vp then rho."""
+    amps = [a / 10 for a in range(-5, 6) if a != 0]
+    idx = (k + 7 * rank) % (2 * len(amps))
+    return amps[idx % len(amps)], ("vp" if idx < len(amps) else "rho")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+def cpu_sample(nt_sample=300, shots=(0,)):
+    """The FP64 oracle on a bounded sample of the workload: the same three calls for the
+    listed shots over the first nt_sample steps.  Returns (Gcell-updates/s, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    from paper_1804_01184_gb300 import inputs as I
+    amp, which = contrast_of(0, 0)
+    w = I.config_gaussian(amp, which, nt=nt_sample)
+    w = w.subset(list(shots))
+    g = oracle.make_grid(**w.grid_kwargs())
+    a0, b0 = w.background()
+    t0 = time.perf_counter()
+    data = oracle.model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    oracle.gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data.astype(np.float32))
+    oracle.born(g, w.pz, a0, b0, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    dt = time.perf_counter() - t0
+    cells = w.Nx * w.Nz * w.nt * w.ns * 4
+    return cells / dt / 1e9, dt, cells
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    nt_s = 200
+    for _ in range(args.warmup):
+        cpu_sample(nt_s)
+    times, cells = [], 0
+    for _ in range(args.steps):
+        _, dt, cells = cpu_sample(nt_s)
+        times.append(dt)
+    total = sum(times)
+    value = cells * args.steps / total / 1e9
+    sample = f"1 of 64 shots, first {nt_s} of 3000 steps, full 681x681 grid: model + gradient + born (FP64 C oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gaussian-601x601-o8 (bounded oracle sample)", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1804_01184_gb300 import fwi
+    from paper_1804_01184_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    fwi.lib()
+
+    nt, ns = args.nt, args.shots
+    w0 = I.config_gaussian(0.3, "vp", nt=nt, ns=ns)
+    g = fwi.make_grid(**w0.grid_kwargs())
+    nr = w0.nr
+    src = torch.from_numpy(w0.src_xy).to(dev)
+    rec = torch.from_numpy(w0.rec_xy).to(dev)
+    wav = torch.from_numpy(w0.wavelet).to(dev)
+    zero = torch.zeros((w0.nz, w0.nx), dtype=torch.float32, device=dev)
+
+    # the contrasts of every step, resident in HBM before the timed region
+    nsteps = args.warmup + args.steps
+    models = []
+    for k in range(nsteps):
+        amp, which = contrast_of(k, rank)
+        wk = I.config_gaussian(amp, which, nt=nt, ns=ns)
+        models.append((torch.from_numpy(wk.xi_a).to(dev), torch.from_numpy(wk.xi_b).to(dev)))
+
+    ws_model = fwi.workspace(g, ns, nr, fwi.OP_MODEL)
+    ws_born = fwi.workspace(g, ns, nr, fwi.OP_BORN)
+    data = torch.empty((ns, nr, nt), dtype=torch.float32, device=dev)
+    dtr = torch.empty_like(data)
+    grads = torch.empty((5, 2, w0.nz, w0.nx), dtype=torch.float64, device=dev)
+    misfit = torch.empty((), dtype=torch.float64, device=dev)
+    ws_grad = fwi.workspace(g, ns, nr, fwi.OP_GRADIENT)
+    stream = torch.cuda.current_stream(dev)
+    launches = [0]
+
+    def step(k, check=False):
+        xa, xb = models[k]
+        fwi.fwi_model(g, w0.pz, xa, xb, src, wav, rec, traces=data, work=ws_model, check=check)
+        launches[0] += fwi.launch_count()
+        fwi.fwi_gradient(g, w0.pz, zero, zero, src, wav, rec, data, misfit=misfit, grads=grads,
+                         work=ws_grad, check=check)
+        launches[0] += fwi.launch_count()
+        fwi.fwi_born(g, w0.pz, zero, zero, xa, xb, src, wav, rec, dtraces=dtr, work=ws_born, check=check)
+        launches[0] += fwi.launch_count()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for k in range(args.warmup):
+        step(k, check=(k == 0))
+    torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    clocks.start()
+    fwi.lib().fwi_profile(1)
+    launches[0] = 0
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.warmup, nsteps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    fwi.lib().fwi_profile(0)
+    clk = clocks.stop()
+    buf = __import__("ctypes").create_string_buffer(1 << 16)
+    fwi.lib().fwi_profile_report(buf, len(buf))
+    prof = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, tot = line.rsplit(" ", 2)
+        prof[name] = (int(cnt), float(tot))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    cells = w0.Nx * w0.Nz
+    upd_per_step = cells * nt * ns * 4            # model 1 + gradient 2 + Born 1
+    value = upd_per_step * args.steps * world / (ms / 1e3) / 1e9
+    grads_per_s = args.steps * world / (ms / 1e3)
+
+    # roofline of the dominant kernel (largest share of device time in the timed region)
+    import json as _j
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = _j.load(open(pk_path))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    kernels = {}
+    total_dev = sum(v[1] for v in prof.values()) or 1.0
+    for name, (cnt, tot) in prof.items():
+        short = name.split("::")[-1].split("<")[0]
+        kernels[name.replace("fwi::", "").replace("(", "").replace(")", "")] = {
+            "launches": cnt, "ms": round(tot, 3), "share": round(tot / total_dev, 4)}
+    if dom:
+        name, (cnt, tot) = dom
+        short = name.split("::")[-1].split("<")[0]
+        key = short + ("<true>" if "true" in name else "<false>" if "false" in name else "")
+        per_cell = KERNEL_BYTES.get(key, KERNEL_BYTES.get(short))
+        if per_cell:
+            # shots per launch: every launch of the timed region covers the whole group
+            B = ns
+            bytes_per_launch = cells * (per_cell * B + MODEL_BYTES.get(short, 0))
+            avg_s = tot / cnt / 1e3
+            achieved = bytes_per_launch / avg_s / 1e9
+            roof = {"kernel": short, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                    "bytes_per_launch": bytes_per_launch, "avg_launch_us": round(avg_s * 1e6, 2),
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "gradients_per_s": round(grads_per_s, 4),
+        "config": {"workload": "gaussian-601x601-o8", "grid": "601x601 + 40-cell sponge = 681x681", "dx_m": 5.0,
+                   "order": 8, "nt": nt, "shots": ns, "receivers": nr,
+                   "step": "fwi_model(true) + fwi_gradient(background, 5 parameterizations) + fwi_born(background)",
+                   "l2": "working set larger than L2 (wavefield state alone %d MB)" % (3 * ns * cells * 4 >> 20),
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "gradient_plan": "workspace %.1f GB" % (ws_grad.numel() / 2**30)},
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches[0] * world, "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_plain:
+        out["plain_per_shot"] = plain_per_shot(fwi, I, g, w0, dev, nt)
+    if not args.no_e2e:
+        out["e2e"] = end_to_end(fwi, I, g, w0, dev, nt, ns, args, rank, world, (ws_model, ws_grad, ws_born))
+    if rank == 0 and not args.no_cpu:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        v, dt, _ = cpu_sample(300)
+        out["cpu_baseline"] = {"value": round(v, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": "1 of 64 shots, first 300 of 3000 steps, full 681x681 grid: model + "
+                                         "gradient + born (FP64 C oracle, %.1f s)" % dt}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def plain_per_shot(fwi, I, g, w0, dev, nt, shots=4):
+    """The same step for a few shots, one shot at a time (workspaces sized for one shot):
+    the plain per-shot GPU path, no batching, no graphs."""
+    import torch
+    sub = w0.subset(range(shots))
+    src = torch.from_numpy(sub.src_xy).to(dev)
+    rec = torch.from_numpy(w0.rec_xy).to(dev)
+    wav = torch.from_numpy(w0.wavelet).to(dev)
+    xa, xb = torch.from_numpy(w0.xi_a).to(dev), torch.from_numpy(w0.xi_b).to(dev)
+    zero = torch.zeros_like(xa)
+    nr = w0.nr
+    wm = fwi.workspace(g, 1, nr, fwi.OP_MODEL, fwi.fwi_workspace_bytes(g, 1, nr, fwi.OP_MODEL, 0))
+    wb = fwi.workspace(g, 1, nr, fwi.OP_BORN, fwi.fwi_workspace_bytes(g, 1, nr, fwi.OP_BORN, 0))
+    wg = fwi.workspace(g, 1, nr, fwi.OP_GRADIENT, fwi.fwi_workspace_bytes(g, 1, nr, fwi.OP_GRADIENT, 1 << 62))
+    data = torch.empty((1, nr, nt), dtype=torch.float32, device=dev)
+    dtr = torch.empty_like(data)
+    grads = torch.empty((5, 2, w0.nz, w0.nx), dtype=torch.float64, device=dev)
+    misfit = torch.empty((), dtype=torch.float64, device=dev)
+
+    def one(s):
+        fwi.fwi_model(g, w0.pz, xa, xb, src[s:s + 1], wav, rec, traces=data, work=wm, check=False)
+        fwi.fwi_gradient(g, w0.pz, zero, zero, src[s:s + 1], wav, rec, data, misfit=misfit, grads=grads, work=wg,
+                         check=False)
+        fwi.fwi_born(g, w0.pz, zero, zero, xa, xb, src[s:s + 1], wav, rec, dtraces=dtr, work=wb, check=False)
+
+    one(0)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for s in range(shots):
+        one(s)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    upd = w0.Nx * w0.Nz * nt * shots * 4
+    return {"value": round(upd / dt / 1e9, 3), "unit": UNIT, "shots": shots,
+            "ms_per_shot": round(1e3 * dt / shots, 2)}
+
+
+def end_to_end(fwi, I, g, w0, dev, nt, ns, args, rank, world, workspaces):
+    """The same step through the public binding with HOST inputs and outputs: every step copies
+    its inputs from pinned host memory and reads every result back, inside the timed region."""
+    import torch
+    amp, which = contrast_of(0, rank)
+    wk = I.config_gaussian(amp, which, nt=nt, ns=ns)
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    h_in = {"xa": pin(wk.xi_a), "xb": pin(wk.xi_b), "src": pin(wk.src_xy), "rec": pin(wk.rec_xy),
+            "wav": pin(wk.wavelet)}
+    nr = wk.nr
+    h_data = torch.empty((ns, nr, nt), dtype=torch.float32).pin_memory()
+    h_dtr = torch.empty_like(h_data).pin_memory()
+    h_grads = torch.empty((5, 2, wk.nz, wk.nx), dtype=torch.float64).pin_memory()
+    h_mis = torch.empty((), dtype=torch.float64).pin_memory()
+    wm, wg, wb = workspaces
+    h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in (h_data, h_dtr, h_grads, h_mis))
+
+    def step():
+        d = {k: v.to(dev, non_blocking=True) for k, v in h_in.items()}
+        zero = torch.zeros_like(d["xa"])
+        data = fwi.fwi_model(g, w0.pz, d["xa"], d["xb"], d["src"], d["wav"], d["rec"], work=wm, check=False)
+        mis, grads = fwi.fwi_gradient(g, w0.pz, zero, zero, d["src"], d["wav"], d["rec"], data, work=wg,
+                                      check=False)
+        dtr = fwi.fwi_born(g, w0.pz, zero, zero, d["xa"], d["xb"], d["src"], d["wav"], d["rec"], work=wb,
+                           check=False)
+        h_data.copy_(data, non_blocking=True)
+        h_grads.copy_(grads, non_blocking=True)
+        h_mis.copy_(mis, non_blocking=True)
+        h_dtr.copy_(dtr, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    step()
+    steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dt], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = t.item()
+    upd = w0.Nx * w0.Nz * nt * ns * 4 * steps * world
+    return {"value": round(upd / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/*
+ * fwi.h -- C ABI of libfwi.so, the GB300 (sm_103a) Scheme III hot path of
+ *   Bharadwaj, Mulder & Drijkoningen, "A parameterization analysis for acoustic
+ *   full-waveform inversion of sub-wavelength anomalies" (arXiv:1804.01184).
+ *
+ * Time-domain staggered-grid finite-difference modelling of the 2-D variable-density
+ * acoustic wave equation (Sec. "Scheme III"; the operator of eq. param_full), its Born
+ * linearisation, and the adjoint wavefield with the zero-lag cross-correlation fused into
+ * the gradient, converted by the chain rule to every parameterization of Table 1
+ * (Sec. "Modelling and Inversion").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every array argument is a DEVICE pointer owned by the caller, except the fwi_grid,
+ *    fwi_sources and fwi_receivers structs themselves (host memory, read during the call).
+ *  - The library allocates nothing.  Scratch memory is the caller's `work` buffer of
+ *    `work_bytes` bytes (256-byte aligned); fwi_workspace_bytes() says how much an
+ *    operation needs.  A larger buffer lets fwi_gradient keep more wavefield history
+ *    (fewer recomputed forward steps); the plan is a deterministic function of the sizes.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream).  Results are valid once the stream has reached them.  Argument errors
+ *    that the host can see return an error code at once; errors that need the data (a
+ *    contrast with 1 + xi <= 0, a CFL violation, a position outside the grid) are recorded
+ *    in the workspace and returned by fwi_status().
+ *  - Grids are row-major [nz][nx], x fastest.  The physical node (ix, iz) sits at
+ *    x = ix*dx, z = iz*dx metres.  The computational grid adds `sponge` absorbing cells on
+ *    every side; those cells take the model of the nearest physical cell.
+ *  - Return value: FWI_OK (0) or a negative FWI_E* code; fwi_last_error() gives a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Work on different streams must use different workspaces.
+ */
+#ifndef FWI_H_
+#define FWI_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FWI_OK        0
+#define FWI_EINVAL   -1   /* bad size, null pointer, 1 + xi <= 0, position off the grid */
+#define FWI_ECFL     -2   /* dt above the stability limit of the stencil for the model */
+#define FWI_ENOMEM   -3   /* workspace smaller than the operation's minimum             */
+#define FWI_ETIMEOUT -4   /* a bounded device-side wait expired                         */
+#define FWI_ECUDA    -5   /* a CUDA runtime call failed                                 */
+
+/* Parameterizations of Table 1; contrasts xi = (m - m_o)/m_o of the named pair. */
+typedef enum {
+    FWI_VP_RHO = 0,      /* (A) P-wave speed, density            */
+    FWI_IP_RHO = 1,      /* (B) impedance Ip = rho vp, density   */
+    FWI_VP_IP = 2,       /* (C) P-wave speed, impedance          */
+    FWI_K_RHO = 3,       /* (D) bulk modulus K = rho vp^2, density */
+    FWI_INVK_INVRHO = 4  /* (E) 1/K, 1/rho                        */
+} fwi_param;
+
+/* Operations, for fwi_workspace_bytes(). */
+typedef enum { FWI_OP_MODEL = 0, FWI_OP_BORN = 1, FWI_OP_ADJOINT = 2, FWI_OP_GRADIENT = 3 } fwi_op;
+
+typedef struct {
+    int nx, nz;        /* physical nodes (>= 2 each)                                      */
+    int sponge;        /* absorbing cells added on each side (>= 0)                       */
+    int order;         /* spatial order of the staggered stencil: 4 or 8                  */
+    int nt;            /* time steps (>= 1)                                               */
+    double dx;         /* grid spacing [m], the same in x and z                           */
+    double dt;         /* time step [s]                                                   */
+    double vp_o;       /* reference P-wave speed [m/s] (homogeneous reference medium)     */
+    double rho_o;      /* reference density [kg/m^3]                                      */
+    double sponge_v;   /* speed used for the sponge profile [m/s] (<= 0: vp_o)            */
+    double sponge_R;   /* target reflection of the sponge (0 < R < 1; <= 0: 1e-3)         */
+} fwi_grid;
+
+/* One point source per shot (explosive: volume injection into the pressure equation,
+ * scaled by the local bulk modulus, bilinear weights / dx^2).  wavelet[n] is the source
+ * time function at t = (n + 1/2) dt, shared by all shots. */
+typedef struct {
+    int ns;                 /* shots                                                   */
+    const float *xy;        /* device [ns][2]: (x, z) in metres                        */
+    const float *wavelet;   /* device [nt]                                             */
+} fwi_sources;
+
+/* Pressure receivers, shared by all shots; sample n of a trace is the bilinear
+ * interpolation of p at time (n + 1) dt. */
+typedef struct {
+    int nr;
+    const float *xy;        /* device [nr][2]: (x, z) in metres                        */
+} fwi_receivers;
+
+/* Bytes of workspace an operation needs.  budget_bytes = 0 asks for the minimum; otherwise
+ * the result is the largest plan that fits in budget_bytes (at least the minimum).  Returns
+ * 0 on invalid arguments. */
+size_t fwi_workspace_bytes(const fwi_grid *g, int ns, int nr, fwi_op op, size_t budget_bytes);
+
+/* Forward modelling (Sec. Scheme III: the forward wavefield of eq. param_full).
+ *   xi_a, xi_b : [nz][nx] float32 contrasts of the model in parameterization pz (Table 1)
+ *   traces     : [ns][nr][nt] float32 output pressure traces
+ * Computes in FP32. */
+int fwi_model(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+              const fwi_sources *src, const fwi_receivers *rec, float *traces,
+              void *work, size_t work_bytes, void *stream);
+
+/* Born modelling: the exact linearisation of fwi_model's discrete scheme around (xi_a, xi_b)
+ * applied to the contrast perturbation (dxi_a, dxi_b) (the Born idea of eq. param_born,
+ * applied to Scheme III's discretisation).  dtraces: [ns][nr][nt] float32. */
+int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+             const float *dxi_a, const float *dxi_b, const fwi_sources *src,
+             const fwi_receivers *rec, float *dtraces, void *work, size_t work_bytes,
+             void *stream);
+
+/* Adjoint modelling: for a trace-space vector residual [ns][nr][nt] (float32) returns the
+ * gradient of sum(residual * traces) w.r.t. the contrasts of all five parameterizations,
+ * grads [5][2][nz][nx] float64 (index [pz][0] = first parameter of pair pz, [pz][1] the
+ * second), evaluated at the model (pz, xi_a, xi_b).  The adjoint wavefield is
+ * cross-correlated with the forward wavefield at every step inside the adjoint kernels
+ * (Sec. "Modelling and Inversion": gradient by adjoint modelling, then the chain rule).
+ * Per-shot, per-step products accumulate in FP32; sums over shots, the density chain rule
+ * and the parameterization chain rules run in FP64. */
+int fwi_adjoint(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+                const fwi_sources *src, const fwi_receivers *rec, const float *residual,
+                double *grads, void *work, size_t work_bytes, void *stream);
+
+/* Misfit and gradient (Sec. "Modelling and Inversion"): J = 1/2 sum (d_mod - data)^2 over
+ * shots, receivers and samples (time-domain reading of the least-squares misfit), written
+ * to misfit (device, 1 float64), and its gradient for all five parameterizations, grads
+ * [5][2][nz][nx] float64.  data: [ns][nr][nt] float32 observed traces. */
+int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+                 const fwi_sources *src, const fwi_receivers *rec, const float *data,
+                 double *misfit, double *grads, void *work, size_t work_bytes, void *stream);
+
+/* Waits for `stream` and returns the data-dependent status recorded by the last operation
+ * that used `work` (FWI_OK, FWI_EINVAL, FWI_ECFL), then clears it. */
+int fwi_status(void *work, void *stream);
+
+/* Message for the last error on this thread ("" if none). */
+const char *fwi_last_error(void);
+
+/* Kernels launched by the last operation on this thread (for launch accounting). */
+long long fwi_launch_count(void);
+
+/* Per-launch timing (no counterpart in the paper: measurement support).  While enabled,
+ * every kernel launch of the library is bracketed by a CUDA event pair recorded on the
+ * launching stream.  fwi_profile_report() waits for those events, writes one line per kernel
+ * "name launches total_ms\n" into buf (at most len bytes, NUL-terminated), resets the
+ * record and returns the report length (or a negative FWI_E* code). */
+int fwi_profile(int enable);
+int fwi_profile_report(char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWI_H_ */

@@ -1,0 +1,627 @@
+// fwi_api.cu -- host side of libfwi.so: argument checks, workspace plans, time loops.
+// The C ABI is declared in include/fwi.h.  Every arithmetic step of the method runs in the
+// kernels of fwi_kernels.cuh; this file only plans memory and orders launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fwi.h"
+#include "fwi_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+thread_local long long g_launches = 0;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+// Optional per-launch timing: an event pair on the launching stream around every kernel,
+// harvested by fwi_profile_report() after the caller has synchronised.
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;     // pairs, reused between reports
+    std::vector<int> kind;           // kernel id of pair k
+    size_t used = 0;                 // pairs recorded since the last report
+    std::map<std::string, int> ids;
+    std::vector<std::string> names;
+
+    int id(const char *name)
+    {
+        auto it = ids.find(name);
+        if (it != ids.end()) return it->second;
+        int k = (int)names.size();
+        ids.emplace(name, k);
+        names.emplace_back(name);
+        return k;
+    }
+    // returns the event pair for the next launch, or nullptr if profiling is off
+    cudaEvent_t *next(const char *name)
+    {
+        if (!on) return nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        if (2 * (used + 1) > ev.size()) {
+            size_t add = std::max<size_t>(1024, ev.size());
+            for (size_t k = 0; k < add; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+                ev.push_back(e);
+            }
+        }
+        kind.resize(used + 1);
+        kind[used] = id(name);
+        return &ev[2 * used++];
+    }
+};
+Profiler g_prof;
+
+constexpr size_t ALIGN = 256;
+constexpr int RED_BLOCKS = 264;   // misfit partial sums per shot group
+
+size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Plan {
+    fwi::Dims d;
+    fwi::Stencil st;
+    int M = 0, ns = 0, nr = 0, nt = 0;
+    int B = 0;        // shots per group
+    int C = 0;        // steps per snapshot segment (== nt: whole history kept)
+    int nseg = 1;     // segments
+    int ngroups = 0;
+    // byte offsets into the workspace
+    size_t status = 0, K = 0, bx = 0, bz = 0, ax = 0, axh = 0, az = 0, azh = 0;
+    size_t sidx = 0, sw = 0, ridx = 0, rw = 0;
+    size_t p = 0, vx = 0, vz = 0;
+    size_t dK = 0, dbx = 0, dbz = 0, dp = 0, dvx = 0, dvz = 0;
+    size_t ap = 0, avx = 0, avz = 0, accK = 0, accBx = 0, accBz = 0, snap = 0, ckpt = 0;
+    size_t gK = 0, hx = 0, hz = 0, traces = 0, partial = 0;
+    size_t total = 0;
+};
+
+bool grid_ok(const fwi_grid *g)
+{
+    return g && g->nx >= 2 && g->nz >= 2 && g->sponge >= 0 && (g->order == 4 || g->order == 8) &&
+           g->nt >= 1 && g->dx > 0 && g->dt > 0 && g->vp_o > 0 && g->rho_o > 0 &&
+           std::isfinite(g->dx) && std::isfinite(g->dt);
+}
+
+// Fills dims / stencil and lays out the workspace for (B, C).
+void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
+{
+    fwi::Dims &d = P.d;
+    d.nx = g->nx; d.nz = g->nz; d.S = g->sponge;
+    d.Nx = g->nx + 2 * g->sponge; d.Nz = g->nz + 2 * g->sponge;
+    d.Px = (int)up((size_t)d.Nx, 32);
+    d.Np = (long long)d.Px * d.Nz;
+    P.M = g->order / 2;
+    static const double c4[2] = {9.0 / 8.0, -1.0 / 24.0};
+    static const double c8[4] = {1225.0 / 1024.0, -245.0 / 3072.0, 49.0 / 5120.0, -5.0 / 7168.0};
+    for (int k = 0; k < 4; ++k) {
+        double c = k < P.M ? (P.M == 2 ? c4[k] : c8[k]) : 0.0;
+        P.st.c[k] = (float)(c * g->dt / g->dx);
+    }
+    P.ns = ns; P.nr = nr; P.nt = g->nt;
+    P.B = std::max(1, std::min(B, std::max(ns, 1)));
+    P.C = std::max(1, std::min(C, g->nt));
+    P.nseg = (g->nt + P.C - 1) / P.C;
+    P.ngroups = ns > 0 ? (ns + P.B - 1) / P.B : 0;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = up(off + bytes, ALIGN); return o; };
+    const size_t F = sizeof(float), D = sizeof(double);
+    const size_t field = (size_t)d.Np * F, bfield = (size_t)P.B * field;
+    P.status = take(ALIGN);
+    P.K = take(field); P.bx = take(field); P.bz = take(field);
+    P.ax = take(d.Px * F); P.axh = take(d.Px * F); P.az = take(d.Nz * F); P.azh = take(d.Nz * F);
+    P.sidx = take(4 * (size_t)std::max(ns, 1) * sizeof(long long));
+    P.sw = take(4 * (size_t)std::max(ns, 1) * F);
+    P.ridx = take(4 * (size_t)std::max(nr, 1) * sizeof(long long));
+    P.rw = take(4 * (size_t)std::max(nr, 1) * F);
+    P.p = take(bfield); P.vx = take(bfield); P.vz = take(bfield);
+    if (op == FWI_OP_BORN) {
+        P.dK = take(field); P.dbx = take(field); P.dbz = take(field);
+        P.dp = take(bfield); P.dvx = take(bfield); P.dvz = take(bfield);
+    }
+    if (op == FWI_OP_ADJOINT || op == FWI_OP_GRADIENT) {
+        P.ap = take(bfield); P.avx = take(bfield); P.avz = take(bfield);
+        P.accK = take(bfield); P.accBx = take(bfield); P.accBz = take(bfield);
+        P.snap = take((size_t)(P.C + 1) * bfield);
+        if (P.nseg > 1) P.ckpt = take((size_t)P.nseg * 3 * bfield);
+        P.gK = take((size_t)d.Np * D); P.hx = take((size_t)d.Np * D); P.hz = take((size_t)d.Np * D);
+    }
+    if (op == FWI_OP_GRADIENT) {
+        P.traces = take((size_t)P.B * std::max(nr, 1) * g->nt * F);
+        P.partial = take((size_t)std::max(P.ngroups, 1) * RED_BLOCKS * D);
+    }
+    P.total = off;
+}
+
+// Chooses (B, C) for the budget: first the whole history for as many shots as fit while a
+// group still fills the GPU (>= 4M cells); then checkpoints every ~sqrt(3 nt) steps with
+// recomputation, for as many shots as fit.  budget 0 -> the minimum plan.
+bool make_plan(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, size_t budget)
+{
+    const int nsm = std::max(ns, 1);
+    const int nt = g->nt;
+    if (op == FWI_OP_MODEL || op == FWI_OP_BORN) {
+        layout(P, g, op, ns, nr, 1, nt);
+        if (budget == 0) return true;
+        if (P.total > budget) return false;
+        for (int B = nsm; B >= 1; --B) {
+            layout(P, g, op, ns, nr, B, nt);
+            if (P.total <= budget) return true;
+        }
+        return false;
+    }
+    Plan tmp;
+    layout(tmp, g, op, ns, nr, 1, nt);
+    const long long Np = tmp.d.Np;
+    const int Cs = std::max(1, (int)std::ceil(std::sqrt(3.0 * nt)));
+    // minimum: one shot, whichever history scheme is smaller
+    Plan a, b;
+    layout(a, g, op, ns, nr, 1, nt);
+    layout(b, g, op, ns, nr, 1, Cs);
+    const Plan &mn = a.total <= b.total ? a : b;
+    if (budget == 0) { P = mn; return true; }
+    if (mn.total > budget) return false;
+    const int Bpar = (int)std::min<long long>(nsm, std::max<long long>(1, (4000000 + Np - 1) / Np));
+    for (int B = nsm; B >= Bpar; --B) {
+        layout(P, g, op, ns, nr, B, nt);
+        if (P.total <= budget) return true;
+    }
+    for (int B = nsm; B >= 1; --B) {
+        layout(P, g, op, ns, nr, B, Cs);
+        if (P.total <= budget) return true;
+    }
+    P = mn;
+    return true;
+}
+
+template <typename T>
+T *at(void *work, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(work) + off); }
+
+int check_common(const fwi_grid *g, const float *xa, const float *xb, const fwi_sources *src,
+                 const fwi_receivers *rec, void *work, size_t work_bytes)
+{
+    if (!grid_ok(g)) return fail(FWI_EINVAL, "invalid grid (nx, nz >= 2, order 4 or 8, nt >= 1, dx, dt, vp_o, rho_o > 0)");
+    if (!xa || !xb) return fail(FWI_EINVAL, "null contrast pointer");
+    if (!src || !rec || src->ns < 0 || rec->nr < 0) return fail(FWI_EINVAL, "invalid sources/receivers");
+    if (src->ns > 0 && (!src->xy || !src->wavelet)) return fail(FWI_EINVAL, "null source arrays");
+    if (rec->nr > 0 && !rec->xy) return fail(FWI_EINVAL, "null receiver array");
+    if (!work) return fail(FWI_EINVAL, "null workspace");
+    if (reinterpret_cast<uintptr_t>(work) % ALIGN) return fail(FWI_EINVAL, "workspace not 256-byte aligned");
+    (void)work_bytes;
+    return FWI_OK;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(FWI_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+#define LAUNCH(kernel, grid, block, smem, stream, ...)             \
+    do {                                                           \
+        cudaEvent_t *ev_ = g_prof.next(#kernel);                   \
+        if (ev_) cudaEventRecord(ev_[0], stream);                  \
+        kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);        \
+        if (ev_) cudaEventRecord(ev_[1], stream);                  \
+        ++g_launches;                                              \
+    } while (0)
+
+dim3 tiles(const fwi::Dims &d, int shots)
+{
+    return dim3((d.Nx + fwi::TX - 1) / fwi::TX, (d.Nz + fwi::TZ - 1) / fwi::TZ, shots);
+}
+const dim3 kBlock(fwi::TX, fwi::NTY);
+
+// Model, sponge tables and acquisition geometry (S1, S2).
+int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float *xb,
+          const fwi_sources *src, const fwi_receivers *rec, void *work, cudaStream_t st)
+{
+    const fwi::Dims &d = P.d;
+    const double sum_c = P.M == 2 ? 9.0 / 8.0 + 1.0 / 24.0
+                                  : 1225.0 / 1024.0 + 245.0 / 3072.0 + 49.0 / 5120.0 + 5.0 / 7168.0;
+    const double cfl = g->dt * std::sqrt(2.0) * sum_c / g->dx;
+    int *status = at<int>(work, P.status);
+    CK(cudaMemsetAsync(status, 0, sizeof(int), st));
+    dim3 b2(32, 8), g2((d.Px + 31) / 32, (d.Nz + 7) / 8);
+    LAUNCH(fwi::k_model, g2, b2, 0, st, xa, xb, pz, g->vp_o, g->rho_o, cfl, d, at<float>(work, P.K),
+           at<float>(work, P.bx), at<float>(work, P.bz), status);
+    const double sv = g->sponge_v > 0 ? g->sponge_v : g->vp_o;
+    const double sR = (g->sponge_R > 0 && g->sponge_R < 1) ? g->sponge_R : 1e-3;
+    LAUNCH(fwi::k_sponge, (d.Px + 127) / 128, 128, 0, st, at<float>(work, P.ax), d.Px, d.nx, d.S, g->dx, g->dt, sv, sR, 0);
+    LAUNCH(fwi::k_sponge, (d.Px + 127) / 128, 128, 0, st, at<float>(work, P.axh), d.Px, d.nx, d.S, g->dx, g->dt, sv, sR, 1);
+    LAUNCH(fwi::k_sponge, (d.Nz + 127) / 128, 128, 0, st, at<float>(work, P.az), d.Nz, d.nz, d.S, g->dx, g->dt, sv, sR, 0);
+    LAUNCH(fwi::k_sponge, (d.Nz + 127) / 128, 128, 0, st, at<float>(work, P.azh), d.Nz, d.nz, d.S, g->dx, g->dt, sv, sR, 1);
+    if (src->ns > 0)
+        LAUNCH(fwi::k_geometry, (src->ns + 127) / 128, 128, 0, st, src->xy, src->ns, d, g->dx,
+               g->dt / (g->dx * g->dx), at<long long>(work, P.sidx), at<float>(work, P.sw), status);
+    if (rec->nr > 0)
+        LAUNCH(fwi::k_geometry, (rec->nr + 127) / 128, 128, 0, st, rec->xy, rec->nr, d, g->dx, 1.0,
+               at<long long>(work, P.ridx), at<float>(work, P.rw), status);
+    return FWI_OK;
+}
+
+struct Fwd {
+    const Plan &P;
+    void *work;
+    cudaStream_t st;
+    const float *wav;
+
+    // one forward step n for the group's shots [s0, s0 + bg)
+    void step(int n, int s0, int bg, float *snap) const
+    {
+        const fwi::Dims &d = P.d;
+        float *p = at<float>(work, P.p), *vx = at<float>(work, P.vx), *vz = at<float>(work, P.vz);
+        const float *K = at<float>(work, P.K), *bx = at<float>(work, P.bx), *bz = at<float>(work, P.bz);
+        const float *ax = at<float>(work, P.ax), *axh = at<float>(work, P.axh);
+        const float *az = at<float>(work, P.az), *azh = at<float>(work, P.azh);
+        const long long *sidx = at<long long>(work, P.sidx) + 4LL * s0;
+        const float *sw = at<float>(work, P.sw) + 4LL * s0;
+        if (P.M == 2) {
+            LAUNCH(fwi::k_fwd_v<2>, tiles(d, bg), kBlock, 0, st, p, vx, vz, bx, bz, ax, axh, az, azh, d, P.st);
+            if (snap)
+                LAUNCH((fwi::k_fwd_p<2, true>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+            else
+                LAUNCH((fwi::k_fwd_p<2, false>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+        } else {
+            LAUNCH(fwi::k_fwd_v<4>, tiles(d, bg), kBlock, 0, st, p, vx, vz, bx, bz, ax, axh, az, azh, d, P.st);
+            if (snap)
+                LAUNCH((fwi::k_fwd_p<4, true>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+            else
+                LAUNCH((fwi::k_fwd_p<4, false>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+        }
+    }
+    void sample(int n, int bg, int nr, float *traces) const
+    {
+        if (nr == 0) return;
+        LAUNCH(fwi::k_sample, (bg * nr + 127) / 128, 128, 0, st, at<float>(work, P.p), bg, nr, P.nt, n, P.d.Np,
+               at<long long>(work, P.ridx), at<float>(work, P.rw), traces);
+    }
+};
+
+int finish(cudaStream_t st)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    (void)st;
+    return FWI_OK;
+}
+
+int plan_for(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, size_t work_bytes)
+{
+    if (!make_plan(P, g, op, ns, nr, work_bytes))
+        return fail(FWI_ENOMEM, "workspace of %zu bytes is below the minimum %zu for this operation",
+                    work_bytes, fwi_workspace_bytes(g, ns, nr, op, 0));
+    return FWI_OK;
+}
+
+// Forward over all steps for one group, used by model, adjoint and gradient.
+//   traces: [bg][nr][nt] output or null;  with_hist: keep snapshots / checkpoints for the adjoint.
+int forward_group(const Plan &P, void *work, cudaStream_t st, const float *wav, int s0, int bg,
+                  float *traces, bool with_hist)
+{
+    const Fwd f{P, work, st, wav};
+    const size_t bf = (size_t)bg * P.d.Np * sizeof(float);
+    CK(cudaMemsetAsync(at<char>(work, P.p), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.vx), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.vz), 0, bf, st));
+    const size_t slot = (size_t)P.B * P.d.Np;   // floats between snapshot slots
+    const int last0 = (P.nseg - 1) * P.C;       // first step of the last segment
+    for (int n = 0; n < P.nt; ++n) {
+        float *snap = nullptr;
+        if (with_hist) {
+            if (P.nseg > 1 && n % P.C == 0) {
+                float *ck = at<float>(work, P.ckpt) + (size_t)(n / P.C) * 3 * slot;
+                CK(cudaMemcpyAsync(ck, at<float>(work, P.p), bf, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(ck + slot, at<float>(work, P.vx), bf, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(ck + 2 * slot, at<float>(work, P.vz), bf, cudaMemcpyDeviceToDevice, st));
+            }
+            if (n == last0)
+                CK(cudaMemcpyAsync(at<float>(work, P.snap), at<float>(work, P.p), bf, cudaMemcpyDeviceToDevice, st));
+            if (n >= last0) snap = at<float>(work, P.snap) + (size_t)(n + 1 - last0) * slot;
+        }
+        f.step(n, s0, bg, snap);
+        if (traces) f.sample(n, bg, P.nr, traces);
+    }
+    return FWI_OK;
+}
+
+// Adjoint over all segments for one group (history from forward_group), accumulating into
+// the per-slot FP32 accumulators.  res: [bg][nr][nt] residual of the group.
+int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, int s0, int bg,
+                  const float *res)
+{
+    const fwi::Dims &d = P.d;
+    const Fwd f{P, work, st, wav};
+    const size_t bf = (size_t)bg * d.Np * sizeof(float);
+    const size_t slot = (size_t)P.B * d.Np;
+    float *ap = at<float>(work, P.ap), *avx = at<float>(work, P.avx), *avz = at<float>(work, P.avz);
+    CK(cudaMemsetAsync(ap, 0, bf, st));
+    CK(cudaMemsetAsync(avx, 0, bf, st));
+    CK(cudaMemsetAsync(avz, 0, bf, st));
+    const float *K = at<float>(work, P.K), *bx = at<float>(work, P.bx), *bz = at<float>(work, P.bz);
+    const float *ax = at<float>(work, P.ax), *axh = at<float>(work, P.axh);
+    const float *az = at<float>(work, P.az), *azh = at<float>(work, P.azh);
+    float *aK = at<float>(work, P.accK), *aBx = at<float>(work, P.accBx), *aBz = at<float>(work, P.accBz);
+    float *snap = at<float>(work, P.snap);
+    for (int k = P.nseg - 1; k >= 0; --k) {
+        const int n0 = k * P.C, n1 = std::min(n0 + P.C, P.nt);
+        if (k < P.nseg - 1) {   // recompute the segment from its checkpoint
+            const float *ck = at<float>(work, P.ckpt) + (size_t)k * 3 * slot;
+            CK(cudaMemcpyAsync(at<float>(work, P.p), ck, bf, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(at<float>(work, P.vx), ck + slot, bf, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(at<float>(work, P.vz), ck + 2 * slot, bf, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(snap, ck, bf, cudaMemcpyDeviceToDevice, st));
+            for (int n = n0; n < n1; ++n) f.step(n, s0, bg, snap + (size_t)(n + 1 - n0) * slot);
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            if (P.nr > 0)
+                LAUNCH(fwi::k_adj_inject, (bg * P.nr + 127) / 128, 128, 0, st, ap, bg, P.nr, P.nt, n, d.Np,
+                       at<long long>(work, P.ridx), at<float>(work, P.rw), res);
+            const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
+            if (P.M == 2) {
+                LAUNCH(fwi::k_adj_v<2>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, K, ax, axh, az, azh, pn, pn1,
+                       aK, aBx, aBz, d, P.st);
+                LAUNCH(fwi::k_adj_p<2>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, bx, bz, ax, az, d, P.st);
+            } else {
+                LAUNCH(fwi::k_adj_v<4>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, K, ax, axh, az, azh, pn, pn1,
+                       aK, aBx, aBz, d, P.st);
+                LAUNCH(fwi::k_adj_p<4>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, bx, bz, ax, az, d, P.st);
+            }
+        }
+    }
+    return FWI_OK;
+}
+
+int finalize_grad(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float *xb, void *work,
+                  double *grads, cudaStream_t st)
+{
+    const fwi::Dims &d = P.d;
+    dim3 b2(32, 8), gp((d.Nx + 31) / 32, (d.Nz + 7) / 8), gq((d.nx + 31) / 32, (d.nz + 7) / 8);
+    LAUNCH(fwi::k_grad_cells, gp, b2, 0, st, at<float>(work, P.accK), at<float>(work, P.accBx),
+           at<float>(work, P.accBz), P.B, at<float>(work, P.K), at<float>(work, P.bx), at<float>(work, P.bz), d,
+           at<double>(work, P.gK), at<double>(work, P.hx), at<double>(work, P.hz));
+    LAUNCH(fwi::k_grad_final, gq, b2, 0, st, at<double>(work, P.gK), at<double>(work, P.hx),
+           at<double>(work, P.hz), xa, xb, pz, g->vp_o, g->rho_o, d, grads);
+    return FWI_OK;
+}
+
+int adjoint_impl(const fwi_grid *g, int pz, const float *xa, const float *xb, const fwi_sources *src,
+                 const fwi_receivers *rec, const float *residual, const float *data, double *misfit,
+                 double *grads, void *work, size_t work_bytes, cudaStream_t st)
+{
+    const fwi_op op = data ? FWI_OP_GRADIENT : FWI_OP_ADJOINT;
+    Plan P;
+    int rc = plan_for(P, g, op, src->ns, rec->nr, work_bytes);
+    if (rc) return rc;
+    if ((rc = setup(P, g, pz, xa, xb, src, rec, work, st))) return rc;
+    const size_t bf = (size_t)P.B * P.d.Np * sizeof(float);
+    CK(cudaMemsetAsync(at<char>(work, P.accK), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.accBx), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.accBz), 0, bf, st));
+    const long long per_shot = (long long)P.nr * P.nt;
+    for (int gi = 0; gi < P.ngroups; ++gi) {
+        const int s0 = gi * P.B, bg = std::min(P.B, P.ns - s0);
+        const float *res;
+        if (data) {
+            float *tr = at<float>(work, P.traces);
+            if ((rc = forward_group(P, work, st, src->wavelet, s0, bg, tr, true))) return rc;
+            const long long n = bg * per_shot;
+            if (n > 0)
+                LAUNCH(fwi::k_residual, RED_BLOCKS, fwi::RED_THREADS, 0, st, tr, data + s0 * per_shot, n,
+                       at<double>(work, P.partial) + (size_t)gi * RED_BLOCKS);
+            else
+                CK(cudaMemsetAsync(at<double>(work, P.partial) + (size_t)gi * RED_BLOCKS, 0,
+                                   RED_BLOCKS * sizeof(double), st));
+            res = tr;
+        } else {
+            if ((rc = forward_group(P, work, st, src->wavelet, s0, bg, nullptr, true))) return rc;
+            res = residual + s0 * per_shot;
+        }
+        if ((rc = adjoint_group(P, work, st, src->wavelet, s0, bg, res))) return rc;
+    }
+    if (data) {
+        if (P.ngroups > 0)
+            LAUNCH(fwi::k_sum_final, 1, fwi::RED_THREADS, 0, st, at<double>(work, P.partial),
+                   P.ngroups * RED_BLOCKS, misfit);
+        else
+            CK(cudaMemsetAsync(misfit, 0, sizeof(double), st));
+    }
+    if ((rc = finalize_grad(P, g, pz, xa, xb, work, grads, st))) return rc;
+    return finish(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fwi_workspace_bytes(const fwi_grid *g, int ns, int nr, fwi_op op, size_t budget_bytes)
+{
+    if (!grid_ok(g) || ns < 0 || nr < 0 || op < FWI_OP_MODEL || op > FWI_OP_GRADIENT) return 0;
+    Plan P;
+    if (!make_plan(P, g, op, ns, nr, budget_bytes)) {
+        make_plan(P, g, op, ns, nr, 0);
+    }
+    return P.total;
+}
+
+int fwi_model(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b, const fwi_sources *src,
+              const fwi_receivers *rec, float *traces, void *work, size_t work_bytes, void *stream)
+{
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_common(g, xi_a, xi_b, src, rec, work, work_bytes);
+    if (rc) return rc;
+    if ((int)pz < 0 || (int)pz > 4) return fail(FWI_EINVAL, "unknown parameterization %d", (int)pz);
+    if (src->ns > 0 && rec->nr > 0 && !traces) return fail(FWI_EINVAL, "null traces");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan P;
+    if ((rc = plan_for(P, g, FWI_OP_MODEL, src->ns, rec->nr, work_bytes))) return rc;
+    if ((rc = setup(P, g, pz, xi_a, xi_b, src, rec, work, st))) return rc;
+    for (int gi = 0; gi < P.ngroups; ++gi) {
+        const int s0 = gi * P.B, bg = std::min(P.B, P.ns - s0);
+        if ((rc = forward_group(P, work, st, src->wavelet, s0, bg, traces + (size_t)s0 * P.nr * P.nt, false))) return rc;
+    }
+    return finish(st);
+}
+
+int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b, const float *dxi_a,
+             const float *dxi_b, const fwi_sources *src, const fwi_receivers *rec, float *dtraces, void *work,
+             size_t work_bytes, void *stream)
+{
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_common(g, xi_a, xi_b, src, rec, work, work_bytes);
+    if (rc) return rc;
+    if ((int)pz < 0 || (int)pz > 4) return fail(FWI_EINVAL, "unknown parameterization %d", (int)pz);
+    if (!dxi_a || !dxi_b) return fail(FWI_EINVAL, "null perturbation pointer");
+    if (src->ns > 0 && rec->nr > 0 && !dtraces) return fail(FWI_EINVAL, "null dtraces");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan P;
+    if ((rc = plan_for(P, g, FWI_OP_BORN, src->ns, rec->nr, work_bytes))) return rc;
+    if ((rc = setup(P, g, pz, xi_a, xi_b, src, rec, work, st))) return rc;
+    const fwi::Dims &d = P.d;
+    dim3 b2(32, 8), g2((d.Px + 31) / 32, (d.Nz + 7) / 8);
+    LAUNCH(fwi::k_model_pert, g2, b2, 0, st, xi_a, xi_b, dxi_a, dxi_b, (int)pz, g->vp_o, g->rho_o, d,
+           at<float>(work, P.dK), at<float>(work, P.dbx), at<float>(work, P.dbz));
+    float *p = at<float>(work, P.p), *vx = at<float>(work, P.vx), *vz = at<float>(work, P.vz);
+    float *dp = at<float>(work, P.dp), *dvx = at<float>(work, P.dvx), *dvz = at<float>(work, P.dvz);
+    const float *K = at<float>(work, P.K), *bx = at<float>(work, P.bx), *bz = at<float>(work, P.bz);
+    const float *dK = at<float>(work, P.dK), *dbx = at<float>(work, P.dbx), *dbz = at<float>(work, P.dbz);
+    const float *ax = at<float>(work, P.ax), *axh = at<float>(work, P.axh);
+    const float *az = at<float>(work, P.az), *azh = at<float>(work, P.azh);
+    for (int gi = 0; gi < P.ngroups; ++gi) {
+        const int s0 = gi * P.B, bg = std::min(P.B, P.ns - s0);
+        const size_t bf = (size_t)bg * d.Np * sizeof(float);
+        for (float *f : {p, vx, vz, dp, dvx, dvz}) CK(cudaMemsetAsync(f, 0, bf, st));
+        const long long *sidx = at<long long>(work, P.sidx) + 4LL * s0;
+        const float *sw = at<float>(work, P.sw) + 4LL * s0;
+        float *out = dtraces + (size_t)s0 * P.nr * P.nt;
+        for (int n = 0; n < P.nt; ++n) {
+            if (P.M == 2) {
+                LAUNCH(fwi::k_born_v<2>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, bx, bz, dbx, dbz, ax, axh, az, azh, d, P.st);
+                LAUNCH(fwi::k_born_p<2>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, K, dK, ax, az, d, P.st, sidx, sw, src->wavelet, n);
+            } else {
+                LAUNCH(fwi::k_born_v<4>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, bx, bz, dbx, dbz, ax, axh, az, azh, d, P.st);
+                LAUNCH(fwi::k_born_p<4>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, K, dK, ax, az, d, P.st, sidx, sw, src->wavelet, n);
+            }
+            if (P.nr > 0)
+                LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, dp, bg, P.nr, P.nt, n, d.Np,
+                       at<long long>(work, P.ridx), at<float>(work, P.rw), out);
+        }
+    }
+    return finish(st);
+}
+
+int fwi_adjoint(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b, const fwi_sources *src,
+                const fwi_receivers *rec, const float *residual, double *grads, void *work, size_t work_bytes,
+                void *stream)
+{
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_common(g, xi_a, xi_b, src, rec, work, work_bytes);
+    if (rc) return rc;
+    if ((int)pz < 0 || (int)pz > 4) return fail(FWI_EINVAL, "unknown parameterization %d", (int)pz);
+    if (!grads) return fail(FWI_EINVAL, "null grads");
+    if (src->ns > 0 && rec->nr > 0 && !residual) return fail(FWI_EINVAL, "null residual");
+    return adjoint_impl(g, pz, xi_a, xi_b, src, rec, residual, nullptr, nullptr, grads, work, work_bytes,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b, const fwi_sources *src,
+                 const fwi_receivers *rec, const float *data, double *misfit, double *grads, void *work,
+                 size_t work_bytes, void *stream)
+{
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_common(g, xi_a, xi_b, src, rec, work, work_bytes);
+    if (rc) return rc;
+    if ((int)pz < 0 || (int)pz > 4) return fail(FWI_EINVAL, "unknown parameterization %d", (int)pz);
+    if (!grads || !misfit) return fail(FWI_EINVAL, "null grads or misfit");
+    if (src->ns > 0 && rec->nr > 0 && !data) return fail(FWI_EINVAL, "null data");
+    static const float dummy = 0.f;
+    return adjoint_impl(g, pz, xi_a, xi_b, src, rec, nullptr, data ? data : &dummy, misfit, grads, work,
+                        work_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int fwi_status(void *work, void *stream)
+{
+    if (!work) return fail(FWI_EINVAL, "null workspace");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, work, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(work, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    if (h & fwi::ST_EINVAL) return fail(FWI_EINVAL, "a contrast has 1 + xi <= 0 or a position lies outside the physical grid");
+    if (h & fwi::ST_ECFL) return fail(FWI_ECFL, "dt exceeds the stability limit of the stencil for this model");
+    return FWI_OK;
+}
+
+const char *fwi_last_error(void) { return g_err.c_str(); }
+
+int fwi_profile(int enable)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = enable != 0;
+    return FWI_OK;
+}
+
+int fwi_profile_report(char *buf, size_t len)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    std::vector<double> ms(g_prof.names.size(), 0.0);
+    std::vector<long long> cnt(g_prof.names.size(), 0);
+    int rc = FWI_OK;
+    for (size_t k = 0; k < g_prof.used; ++k) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(g_prof.ev[2 * k + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, g_prof.ev[2 * k], g_prof.ev[2 * k + 1]);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "profile events"); break; }
+        ms[g_prof.kind[k]] += t;
+        ++cnt[g_prof.kind[k]];
+    }
+    g_prof.used = 0;
+    std::string out;
+    char line[256];
+    for (size_t k = 0; k < g_prof.names.size(); ++k) {
+        if (!cnt[k]) continue;
+        snprintf(line, sizeof line, "%s %lld %.6f\n", g_prof.names[k].c_str(), cnt[k], ms[k]);
+        out += line;
+    }
+    if (buf && len) {
+        strncpy(buf, out.c_str(), len - 1);
+        buf[len - 1] = 0;
+    }
+    return rc ? rc : (int)out.size();
+}
+
+long long fwi_launch_count(void) { return g_launches; }
+
+}  // extern "C"

@@ -1,0 +1,615 @@
+// fwi_kernels.cuh -- device code of libfwi.so (sm_103a).
+//
+// Staggered-grid finite differences of the 2-D variable-density acoustic wave equation
+// (Sec. "Scheme III" of arXiv:1804.01184; the operator of eq. param_full), the Born
+// linearisation of the same scheme, and the adjoint scheme with the gradient fused in.
+//
+// Discretisation (the paper gives none of it; the readings are documented with the API):
+//   p, K on nodes (i, j); vx on (i+1/2, j); vz on (i, j+1/2); zero outside the grid.
+//   D+ f at i+1/2 = (1/dx) sum_k c_k (f[i+k] - f[i-k+1]);  D- g at i = (1/dx) sum_k c_k (g[i+k-1] - g[i-k]).
+//   v^{n+1/2} = d_v (v^{n-1/2} - dt b D+ p^n);  p^{n+1} = d_p (p^n - dt K D-.v^{n+1/2}) + source.
+//   Sponge factors are separable: d(i, j) = a_x(i) a_z(j).
+//
+// Memory layout in HBM: every field is [shot][Nz][Px] float32 with the row pitch Px a
+// multiple of 32 floats (128-byte rows); columns Nx..Px-1 stay zero and count as outside.
+// Model arrays (K, bx, bz) are [Nz][Px], shared by all shots of a launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwi {
+
+constexpr int TX = 32;        // tile width (one warp across)
+constexpr int TZ = 32;        // tile height
+constexpr int NTY = 8;        // threads in z per block (block = 32 x 8)
+constexpr int RZ = TZ / NTY;  // rows per thread
+
+struct Dims {
+    int Nx, Nz, Px;       // computational grid and row pitch
+    int nx, nz, S;        // physical grid and sponge width
+    long long Np;         // Px * Nz: floats per field per shot
+};
+
+// c_k * dt / dx: the stencil weights with the time step and spacing folded in
+struct Stencil {
+    float c[4];
+};
+
+// status bits recorded by the kernels
+enum : int { ST_EINVAL = 1, ST_ECFL = 2 };
+
+__device__ __forceinline__ long long cell(const Dims &d, int i, int j) { return (long long)j * d.Px + i; }
+
+// ------------------------------------------------------------------ model build (S1)
+
+// Contrast pair -> (K, rho) for each parameterization of Table 1 (m = m_o (1 + xi);
+// K = rho vp^2, Ip = rho vp).  Returns false when a contrast leaves 1 + xi <= 0.
+__device__ __forceinline__ bool kr_of(int pz, double a, double b, double vp_o, double rho_o,
+                                      double &K, double &rho)
+{
+    if (!(a > -1.0) || !(b > -1.0)) return false;
+    const double Ko = rho_o * vp_o * vp_o, Io = rho_o * vp_o;
+    switch (pz) {
+    case 0: { double v = vp_o * (1.0 + a); rho = rho_o * (1.0 + b); K = rho * v * v; return true; }
+    case 1: { double ip = Io * (1.0 + a); rho = rho_o * (1.0 + b); K = ip * ip / rho; return true; }
+    case 2: { double v = vp_o * (1.0 + a), ip = Io * (1.0 + b); rho = ip / v; K = ip * v; return true; }
+    case 3: K = Ko * (1.0 + a); rho = rho_o * (1.0 + b); return true;
+    case 4: K = Ko / (1.0 + a); rho = rho_o / (1.0 + b); return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// K, bx = 2/(rho_i + rho_{i+1}), bz likewise, on the padded grid (padding copies the
+// nearest physical cell; the last node reuses its own rho).  Checks 1 + xi > 0 and the
+// CFL bound dt vp sqrt(2) sum|c_k| / dx <= 1.
+__global__ void k_model(const float *__restrict__ xa, const float *__restrict__ xb, int pz,
+                        double vp_o, double rho_o, double cfl_coef, Dims d,
+                        float *__restrict__ K, float *__restrict__ bx, float *__restrict__ bz,
+                        int *status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= d.Px || j >= d.Nz) return;
+    const long long o = cell(d, i, j);
+    if (i >= d.Nx) { K[o] = 0.f; bx[o] = 0.f; bz[o] = 0.f; return; }
+    auto phys = [&](int ii, int jj, double &Kv, double &rv) {
+        int pi = clampi(ii - d.S, 0, d.nx - 1), pj = clampi(jj - d.S, 0, d.nz - 1);
+        long long q = (long long)pj * d.nx + pi;
+        return kr_of(pz, xa[q], xb[q], vp_o, rho_o, Kv, rv);
+    };
+    double Kc, rc, Kx, rx, Kz, rz;
+    bool ok = phys(i, j, Kc, rc);
+    ok = phys(i + 1 < d.Nx ? i + 1 : i, j, Kx, rx) && ok;
+    ok = phys(i, j + 1 < d.Nz ? j + 1 : j, Kz, rz) && ok;
+    if (!ok) { atomicOr(status, ST_EINVAL); K[o] = 0.f; bx[o] = 0.f; bz[o] = 0.f; return; }
+    if (sqrt(Kc / rc) * cfl_coef > 1.0) atomicOr(status, ST_ECFL);
+    K[o] = (float)Kc;
+    bx[o] = (float)(2.0 / (rc + rx));
+    bz[o] = (float)(2.0 / (rc + rz));
+}
+
+// Born perturbation of the model: dK = J dxi, drho likewise (Jacobian of the map above),
+// dbx = -bx^2/2 (drho_i + drho_{i+1}), dbz likewise.
+__device__ __forceinline__ void jac_of(int pz, double a, double b, double vp_o, double rho_o,
+                                       double &dKa, double &dKb, double &dra, double &drb)
+{
+    const double Ko = rho_o * vp_o * vp_o, Io = rho_o * vp_o;
+    switch (pz) {
+    case 0: { double v = vp_o * (1.0 + a), r = rho_o * (1.0 + b);
+              dKa = 2.0 * r * v * vp_o; dKb = rho_o * v * v; dra = 0.0; drb = rho_o; break; }
+    case 1: { double ip = Io * (1.0 + a), r = rho_o * (1.0 + b);
+              dKa = 2.0 * ip * Io / r; dKb = -ip * ip * rho_o / (r * r); dra = 0.0; drb = rho_o; break; }
+    case 2: { double v = vp_o * (1.0 + a), ip = Io * (1.0 + b);
+              dKa = ip * vp_o; dKb = Io * v; dra = -ip * vp_o / (v * v); drb = Io / v; break; }
+    case 3: dKa = Ko; dKb = 0.0; dra = 0.0; drb = rho_o; break;
+    default: dKa = -Ko / ((1.0 + a) * (1.0 + a)); dKb = 0.0; dra = 0.0;
+             drb = -rho_o / ((1.0 + b) * (1.0 + b)); break;
+    }
+}
+
+__global__ void k_model_pert(const float *__restrict__ xa, const float *__restrict__ xb,
+                             const float *__restrict__ da, const float *__restrict__ db, int pz,
+                             double vp_o, double rho_o, Dims d, float *__restrict__ dK,
+                             float *__restrict__ dbx, float *__restrict__ dbz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= d.Px || j >= d.Nz) return;
+    const long long o = cell(d, i, j);
+    if (i >= d.Nx) { dK[o] = 0.f; dbx[o] = 0.f; dbz[o] = 0.f; return; }
+    auto pert = [&](int ii, int jj, double &dKv, double &drv, double &rv) {
+        int pi = clampi(ii - d.S, 0, d.nx - 1), pj = clampi(jj - d.S, 0, d.nz - 1);
+        long long q = (long long)pj * d.nx + pi;
+        double a = xa[q], b = xb[q], Kv, j0, j1, j2, j3;
+        kr_of(pz, a, b, vp_o, rho_o, Kv, rv);
+        jac_of(pz, a, b, vp_o, rho_o, j0, j1, j2, j3);
+        dKv = j0 * da[q] + j1 * db[q];
+        drv = j2 * da[q] + j3 * db[q];
+    };
+    double dKc, drc, rc, t, drx, rx, drz, rz;
+    pert(i, j, dKc, drc, rc);
+    pert(i + 1 < d.Nx ? i + 1 : i, j, t, drx, rx);
+    pert(i, j + 1 < d.Nz ? j + 1 : j, t, drz, rz);
+    const double bxv = 2.0 / (rc + rx), bzv = 2.0 / (rc + rz);
+    dK[o] = (float)dKc;
+    dbx[o] = (float)(-0.5 * bxv * bxv * (drc + drx));
+    dbz[o] = (float)(-0.5 * bzv * bzv * (drc + drz));
+}
+
+// Sponge profile along one axis: n physical nodes, S cells each side; half = 1 for the
+// half nodes.  sigma = sigma_max (delta/S)^2, sigma_max = 3 v ln(1/R) / (2 S dx), d = exp(-sigma dt).
+__global__ void k_sponge(float *__restrict__ out, int len, int n, int S, double dx, double dt,
+                         double v, double R, int half)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    const int N = n + 2 * S;
+    if (i >= N) { out[i] = 0.f; return; }
+    const double u = i + (half ? 0.5 : 0.0);
+    double delta = 0.0;
+    if (u < S) delta = S - u;
+    if (u > S + n - 1) delta = u - (S + n - 1);
+    if (S == 0 || delta == 0.0) { out[i] = 1.f; return; }
+    const double smax = 3.0 * v * log(1.0 / R) / (2.0 * S * dx);
+    const double q = delta / S;
+    out[i] = (float)exp(-smax * q * q * dt);
+}
+
+// Bilinear footprint of point k: four (cell offset, weight * scale) pairs.  A point on the
+// last node puts its weight on (i0 + 1).  Points outside the physical grid flag EINVAL.
+__global__ void k_geometry(const float *__restrict__ xy, int n, Dims d, double dx, double scale,
+                           long long *__restrict__ idx, float *__restrict__ w, int *status)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double x = xy[2 * k], z = xy[2 * k + 1];
+    if (!(x >= 0.0 && z >= 0.0 && x <= (d.nx - 1) * dx && z <= (d.nz - 1) * dx)) {
+        atomicOr(status, ST_EINVAL);
+        for (int c = 0; c < 4; ++c) { idx[4 * k + c] = 0; w[4 * k + c] = 0.f; }
+        return;
+    }
+    const double fx = x / dx + d.S, fz = z / dx + d.S;
+    int i0 = (int)floor(fx), j0 = (int)floor(fz);
+    if (i0 > d.Nx - 2) i0 = d.Nx - 2;
+    if (j0 > d.Nz - 2) j0 = d.Nz - 2;
+    const double tx = fx - i0, tz = fz - j0;
+    idx[4 * k + 0] = cell(d, i0, j0);          w[4 * k + 0] = (float)(scale * (1.0 - tx) * (1.0 - tz));
+    idx[4 * k + 1] = cell(d, i0 + 1, j0);      w[4 * k + 1] = (float)(scale * tx * (1.0 - tz));
+    idx[4 * k + 2] = cell(d, i0, j0 + 1);      w[4 * k + 2] = (float)(scale * (1.0 - tx) * tz);
+    idx[4 * k + 3] = cell(d, i0 + 1, j0 + 1);  w[4 * k + 3] = (float)(scale * tx * tz);
+}
+
+// ------------------------------------------------------------- tile loads (shared memory)
+
+// Loads rows [z0 + r0, z0 + r0 + H) x cols [x0 + c0, x0 + c0 + W) of field f (one shot)
+// into s[H][W], zero outside the computational grid; optionally multiplied by a
+// per-cell factor fn(i, j, value).
+template <int H, int W, typename F>
+__device__ __forceinline__ void load_tile(float (&s)[H][W], const float *__restrict__ f, const Dims &d,
+                                          int x0, int z0, int c0, int r0, F fn)
+{
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int t = tid; t < H * W; t += TX * NTY) {
+        const int r = t / W, c = t - r * W;
+        const int gz = z0 + r0 + r, gx = x0 + c0 + c;
+        float v = 0.f;
+        if (gz >= 0 && gz < d.Nz && gx >= 0 && gx < d.Nx) v = fn(gx, gz, __ldg(f + cell(d, gx, gz)));
+        s[r][c] = v;
+    }
+}
+
+struct Ident {
+    __device__ __forceinline__ float operator()(int, int, float v) const { return v; }
+};
+
+// ------------------------------------------------------------------ forward step (S3)
+
+// Velocity half step: v^{n+1/2} = d_v (v^{n-1/2} - dt b D+ p^n) for all shots (blockIdx.z).
+template <int M>
+__global__ void __launch_bounds__(TX *NTY) k_fwd_v(const float *__restrict__ p, float *__restrict__ vx,
+                                                  float *__restrict__ vz, const float *__restrict__ bx,
+                                                  const float *__restrict__ bz,
+                                                  const float *__restrict__ ax, const float *__restrict__ axh,
+                                                  const float *__restrict__ az, const float *__restrict__ azh,
+                                                  Dims d, Stencil st)
+{
+    constexpr int H = TZ + 2 * M - 1, W = TX + 2 * M - 1;
+    __shared__ float sp[H][W];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const long long so = (long long)blockIdx.z * d.Np;
+    load_tile(sp, p + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
+    __syncthreads();
+    const int lx = threadIdx.x, gx = x0 + lx;
+    if (gx >= d.Nx) return;
+    const float axv = ax[gx], axhv = axh[gx];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
+        if (gz >= d.Nz) break;
+        float gxp = 0.f, gzp = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            gxp += st.c[k - 1] * (sp[lz + M - 1][lx + M - 1 + k] - sp[lz + M - 1][lx + M - k]);
+            gzp += st.c[k - 1] * (sp[lz + M - 1 + k][lx + M - 1] - sp[lz + M - k][lx + M - 1]);
+        }
+        const long long m = cell(d, gx, gz), o = so + m;
+        vx[o] = axhv * az[gz] * (vx[o] - bx[m] * gxp);
+        vz[o] = axv * azh[gz] * (vz[o] - bz[m] * gzp);
+    }
+}
+
+// Pressure step: p^{n+1} = d_p (p^n - dt K D-.v^{n+1/2}) + dt K w_n beta / dx^2 at the
+// source cells of the shot; optionally stores p^{n+1} as a snapshot.
+template <int M, bool SNAP>
+__global__ void __launch_bounds__(TX *NTY) k_fwd_p(float *__restrict__ p, const float *__restrict__ vx,
+                                                  const float *__restrict__ vz, const float *__restrict__ K,
+                                                  const float *__restrict__ ax, const float *__restrict__ az,
+                                                  Dims d, Stencil st, const long long *__restrict__ sidx,
+                                                  const float *__restrict__ sw, const float *__restrict__ wav,
+                                                  int n, float *__restrict__ snap)
+{
+    __shared__ float sx[TZ][TX + 2 * M - 1];
+    __shared__ float sz[TZ + 2 * M - 1][TX];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, s = blockIdx.z;
+    const long long so = (long long)s * d.Np;
+    load_tile(sx, vx + so, d, x0, z0, -M, 0, Ident());
+    load_tile(sz, vz + so, d, x0, z0, 0, -M, Ident());
+    __syncthreads();
+    const int lx = threadIdx.x, gx = x0 + lx;
+    if (gx >= d.Nx) return;
+    long long si[4];
+    float swv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { si[c] = sidx[4 * s + c]; swv[c] = sw[4 * s + c]; }
+    const float axv = ax[gx];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
+        if (gz >= d.Nz) break;
+        float dv = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            dv += st.c[k - 1] * (sx[lz][lx + M + k - 1] - sx[lz][lx + M - k]);
+            dv += st.c[k - 1] * (sz[lz + M + k - 1][lx] - sz[lz + M - k][lx]);
+        }
+        const long long m = cell(d, gx, gz), o = so + m;
+        const float Kv = K[m];
+        float pn = axv * az[gz] * (p[o] - Kv * dv);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (si[c] == m) pn += Kv * __ldg(wav + n) * swv[c];
+        p[o] = pn;
+        if (SNAP) snap[o] = pn;
+    }
+}
+
+// trace[s][r][n] = sum_c beta_rc p^{n+1}[cell_rc]
+__global__ void k_sample(const float *__restrict__ p, int ns, int nr, int nt, int n, long long Np,
+                         const long long *__restrict__ ridx, const float *__restrict__ rw,
+                         float *__restrict__ traces)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns * nr) return;
+    const int s = t / nr, r = t - s * nr;
+    const float *ps = p + (long long)s * Np;
+    float v = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v += rw[4 * r + c] * ps[ridx[4 * r + c]];
+    traces[(long long)t * nt + n] = v;
+}
+
+// ------------------------------------------------------------------------ Born (S6)
+
+// Background and scattered velocities together:
+//   dv^{n+1/2} = d_v (dv^{n-1/2} - dt b D+ dp^n - dt db D+ p^n),  v^{n+1/2} as in k_fwd_v.
+template <int M>
+__global__ void __launch_bounds__(TX *NTY) k_born_v(const float *__restrict__ p, float *__restrict__ vx,
+                                                   float *__restrict__ vz, const float *__restrict__ dp,
+                                                   float *__restrict__ dvx, float *__restrict__ dvz,
+                                                   const float *__restrict__ bx, const float *__restrict__ bz,
+                                                   const float *__restrict__ dbx, const float *__restrict__ dbz,
+                                                   const float *__restrict__ ax, const float *__restrict__ axh,
+                                                   const float *__restrict__ az, const float *__restrict__ azh,
+                                                   Dims d, Stencil st)
+{
+    constexpr int H = TZ + 2 * M - 1, W = TX + 2 * M - 1;
+    __shared__ float sp[H][W];
+    __shared__ float sd[H][W];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const long long so = (long long)blockIdx.z * d.Np;
+    load_tile(sp, p + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
+    load_tile(sd, dp + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
+    __syncthreads();
+    const int lx = threadIdx.x, gx = x0 + lx;
+    if (gx >= d.Nx) return;
+    const float axv = ax[gx], axhv = axh[gx];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
+        if (gz >= d.Nz) break;
+        float gxp = 0.f, gzp = 0.f, gxd = 0.f, gzd = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            gxp += st.c[k - 1] * (sp[lz + M - 1][lx + M - 1 + k] - sp[lz + M - 1][lx + M - k]);
+            gzp += st.c[k - 1] * (sp[lz + M - 1 + k][lx + M - 1] - sp[lz + M - k][lx + M - 1]);
+            gxd += st.c[k - 1] * (sd[lz + M - 1][lx + M - 1 + k] - sd[lz + M - 1][lx + M - k]);
+            gzd += st.c[k - 1] * (sd[lz + M - 1 + k][lx + M - 1] - sd[lz + M - k][lx + M - 1]);
+        }
+        const long long m = cell(d, gx, gz), o = so + m;
+        const float fvx = axhv * az[gz], fvz = axv * azh[gz];
+        dvx[o] = fvx * (dvx[o] - bx[m] * gxd - dbx[m] * gxp);
+        dvz[o] = fvz * (dvz[o] - bz[m] * gzd - dbz[m] * gzp);
+        vx[o] = fvx * (vx[o] - bx[m] * gxp);
+        vz[o] = fvz * (vz[o] - bz[m] * gzp);
+    }
+}
+
+//   dp^{n+1} = d_p (dp^n - dt K D-.dv^{n+1/2} - dt dK D-.v^{n+1/2}) + dt dK w_n beta/dx^2
+template <int M>
+__global__ void __launch_bounds__(TX *NTY) k_born_p(float *__restrict__ p, const float *__restrict__ vx,
+                                                   const float *__restrict__ vz, float *__restrict__ dp,
+                                                   const float *__restrict__ dvx, const float *__restrict__ dvz,
+                                                   const float *__restrict__ K, const float *__restrict__ dK,
+                                                   const float *__restrict__ ax, const float *__restrict__ az,
+                                                   Dims d, Stencil st, const long long *__restrict__ sidx,
+                                                   const float *__restrict__ sw, const float *__restrict__ wav, int n)
+{
+    __shared__ float sx[TZ][TX + 2 * M - 1];
+    __shared__ float sz[TZ + 2 * M - 1][TX];
+    __shared__ float sdx[TZ][TX + 2 * M - 1];
+    __shared__ float sdz[TZ + 2 * M - 1][TX];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, s = blockIdx.z;
+    const long long so = (long long)s * d.Np;
+    load_tile(sx, vx + so, d, x0, z0, -M, 0, Ident());
+    load_tile(sz, vz + so, d, x0, z0, 0, -M, Ident());
+    load_tile(sdx, dvx + so, d, x0, z0, -M, 0, Ident());
+    load_tile(sdz, dvz + so, d, x0, z0, 0, -M, Ident());
+    __syncthreads();
+    const int lx = threadIdx.x, gx = x0 + lx;
+    if (gx >= d.Nx) return;
+    long long si[4];
+    float swv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { si[c] = sidx[4 * s + c]; swv[c] = sw[4 * s + c]; }
+    const float axv = ax[gx];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
+        if (gz >= d.Nz) break;
+        float dv = 0.f, ddv = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            dv += st.c[k - 1] * (sx[lz][lx + M + k - 1] - sx[lz][lx + M - k]);
+            dv += st.c[k - 1] * (sz[lz + M + k - 1][lx] - sz[lz + M - k][lx]);
+            ddv += st.c[k - 1] * (sdx[lz][lx + M + k - 1] - sdx[lz][lx + M - k]);
+            ddv += st.c[k - 1] * (sdz[lz + M + k - 1][lx] - sdz[lz + M - k][lx]);
+        }
+        const long long m = cell(d, gx, gz), o = so + m;
+        const float Kv = K[m], dKv = dK[m], f = axv * az[gz];
+        float pn = f * (p[o] - Kv * dv);
+        float dpn = f * (dp[o] - Kv * ddv - dKv * dv);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (si[c] == m) {
+                const float wn = __ldg(wav + n);
+                pn += Kv * wn * swv[c];
+                dpn += dKv * wn * swv[c];
+            }
+        p[o] = pn;
+        dp[o] = dpn;
+    }
+}
+
+// --------------------------------------------------------------- adjoint + gradient (S7)
+
+// pbar^{n+1} += R^T r_n: residual injection at the receivers (one thread per shot/receiver).
+__global__ void k_adj_inject(float *__restrict__ ap, int ns, int nr, int nt, int n, long long Np,
+                             const long long *__restrict__ ridx, const float *__restrict__ rw,
+                             const float *__restrict__ res)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns * nr) return;
+    const int s = t / nr, r = t - s * nr;
+    const float v = res[(long long)t * nt + n];
+    float *as = ap + (long long)s * Np;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) atomicAdd(as + ridx[4 * r + c], rw[4 * r + c] * v);
+}
+
+// Adjoint velocity step with the fused cross-correlation:
+//   q = d_p pbar^{n+1};  vbar += dt D+ (K q);  u = d_v vbar  (stored as the new vbar)
+//   accB += u * dt D+ p^n          (g_b = -sum u dt D+ p^n)
+//   accK += pbar^{n+1} (p^{n+1} - d_p p^n)   (g_K = sum / K: the K-derivative of the step,
+//                                             source term included)
+template <int M>
+__global__ void __launch_bounds__(TX *NTY) k_adj_v(const float *__restrict__ ap, float *__restrict__ avx,
+                                                  float *__restrict__ avz, const float *__restrict__ K,
+                                                  const float *__restrict__ ax, const float *__restrict__ axh,
+                                                  const float *__restrict__ az, const float *__restrict__ azh,
+                                                  const float *__restrict__ pn, const float *__restrict__ pn1,
+                                                  float *__restrict__ accK, float *__restrict__ accBx,
+                                                  float *__restrict__ accBz, Dims d, Stencil st)
+{
+    constexpr int H = TZ + 2 * M - 1, W = TX + 2 * M - 1;
+    __shared__ float sq[H][W];
+    __shared__ float sp[H][W];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const long long so = (long long)blockIdx.z * d.Np;
+    load_tile(sq, ap + so, d, x0, z0, -(M - 1), -(M - 1),
+              [&](int i, int j, float v) { return K[cell(d, i, j)] * (ax[i] * az[j]) * v; });
+    load_tile(sp, pn + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
+    __syncthreads();
+    const int lx = threadIdx.x, gx = x0 + lx;
+    if (gx >= d.Nx) return;
+    const float axv = ax[gx], axhv = axh[gx];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
+        if (gz >= d.Nz) break;
+        float gxq = 0.f, gzq = 0.f, gxp = 0.f, gzp = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            gxq += st.c[k - 1] * (sq[lz + M - 1][lx + M - 1 + k] - sq[lz + M - 1][lx + M - k]);
+            gzq += st.c[k - 1] * (sq[lz + M - 1 + k][lx + M - 1] - sq[lz + M - k][lx + M - 1]);
+            gxp += st.c[k - 1] * (sp[lz + M - 1][lx + M - 1 + k] - sp[lz + M - 1][lx + M - k]);
+            gzp += st.c[k - 1] * (sp[lz + M - 1 + k][lx + M - 1] - sp[lz + M - k][lx + M - 1]);
+        }
+        const long long m = cell(d, gx, gz), o = so + m;
+        const float ux = axhv * az[gz] * (avx[o] + gxq);
+        const float uz = axv * azh[gz] * (avz[o] + gzq);
+        avx[o] = ux;
+        avz[o] = uz;
+        accBx[o] += ux * gxp;
+        accBz[o] += uz * gzp;
+        const float pc = sp[lz + M - 1][lx + M - 1];
+        accK[o] += ap[o] * (pn1[o] - axv * az[gz] * pc);
+    }
+}
+
+// Adjoint pressure step: pbar^n = d_p pbar^{n+1} + dt D- (b u).
+template <int M>
+__global__ void __launch_bounds__(TX *NTY) k_adj_p(float *__restrict__ ap, const float *__restrict__ avx,
+                                                  const float *__restrict__ avz, const float *__restrict__ bx,
+                                                  const float *__restrict__ bz, const float *__restrict__ ax,
+                                                  const float *__restrict__ az, Dims d, Stencil st)
+{
+    __shared__ float sx[TZ][TX + 2 * M - 1];
+    __shared__ float sz[TZ + 2 * M - 1][TX];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const long long so = (long long)blockIdx.z * d.Np;
+    load_tile(sx, avx + so, d, x0, z0, -M, 0, [&](int i, int j, float v) { return bx[cell(d, i, j)] * v; });
+    load_tile(sz, avz + so, d, x0, z0, 0, -M, [&](int i, int j, float v) { return bz[cell(d, i, j)] * v; });
+    __syncthreads();
+    const int lx = threadIdx.x, gx = x0 + lx;
+    if (gx >= d.Nx) return;
+    const float axv = ax[gx];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
+        if (gz >= d.Nz) break;
+        float dv = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            dv += st.c[k - 1] * (sx[lz][lx + M + k - 1] - sx[lz][lx + M - k]);
+            dv += st.c[k - 1] * (sz[lz + M + k - 1][lx] - sz[lz + M - k][lx]);
+        }
+        const long long o = so + cell(d, gx, gz);
+        ap[o] = axv * az[gz] * ap[o] + dv;
+    }
+}
+
+// ------------------------------------------------------------------ reductions (S5, S8)
+
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[RED_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = l < RED_THREADS / 32 ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// r = traces - data (in place in `tr`), partial[blockIdx.x] = 1/2 sum r^2 (FP64).
+__global__ void __launch_bounds__(RED_THREADS) k_residual(float *__restrict__ tr, const float *__restrict__ data,
+                                                          long long n, double *__restrict__ partial)
+{
+    double acc = 0.0;
+    for (long long k = (long long)blockIdx.x * RED_THREADS + threadIdx.x; k < n;
+         k += (long long)gridDim.x * RED_THREADS) {
+        const float r = tr[k] - data[k];
+        tr[k] = r;
+        acc += 0.5 * (double)r * (double)r;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// out[0] = sum of partial[0..n) in a fixed order (single block).
+__global__ void __launch_bounds__(RED_THREADS) k_sum_final(const double *__restrict__ partial, int n,
+                                                           double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += RED_THREADS) acc += partial[k];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[0] = acc;
+}
+
+// Per padded cell, FP64: gK = sum_s accK / K;  hx = g_bx * d bx/d rho_each = (sum_s accBx) bx^2/2
+// (g_bx = -sum accBx, d bx / d rho = -bx^2/2 for each of its two cells), hz likewise.
+__global__ void k_grad_cells(const float *__restrict__ accK, const float *__restrict__ accBx,
+                             const float *__restrict__ accBz, int nslots, const float *__restrict__ K,
+                             const float *__restrict__ bx, const float *__restrict__ bz, Dims d,
+                             double *__restrict__ gK, double *__restrict__ hx, double *__restrict__ hz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= d.Nx || j >= d.Nz) return;
+    const long long m = cell(d, i, j);
+    double sK = 0.0, sx = 0.0, sz = 0.0;
+    for (int s = 0; s < nslots; ++s) {
+        sK += accK[s * d.Np + m];
+        sx += accBx[s * d.Np + m];
+        sz += accBz[s * d.Np + m];
+    }
+    const double b1 = bx[m], b2 = bz[m];
+    gK[m] = sK / (double)K[m];
+    hx[m] = 0.5 * b1 * b1 * sx;
+    hz[m] = 0.5 * b2 * b2 * sz;
+}
+
+// Per physical cell: fold the padding it feeds, form g_rho from the buoyancy nodes that
+// touch each padded cell, then the chain rule of every parameterization at the cell's
+// (K, rho) (closed-form Jacobians of the maps of Table 1), written as grads[5][2][nz][nx].
+__global__ void k_grad_final(const double *__restrict__ gK, const double *__restrict__ hx,
+                             const double *__restrict__ hz, const float *__restrict__ xa,
+                             const float *__restrict__ xb, int pz, double vp_o, double rho_o, Dims d,
+                             double *__restrict__ grads)
+{
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x, pj = blockIdx.y * blockDim.y + threadIdx.y;
+    if (pi >= d.nx || pj >= d.nz) return;
+    const int ilo = pi == 0 ? 0 : pi + d.S, ihi = pi == d.nx - 1 ? d.Nx - 1 : pi + d.S;
+    const int jlo = pj == 0 ? 0 : pj + d.S, jhi = pj == d.nz - 1 ? d.Nz - 1 : pj + d.S;
+    double sK = 0.0, sR = 0.0;
+    for (int j = jlo; j <= jhi; ++j)
+        for (int i = ilo; i <= ihi; ++i) {
+            const long long m = cell(d, i, j);
+            sK += gK[m];
+            double gr = hx[m] + hz[m];                       // buoyancy nodes at i+1/2, j+1/2
+            if (i > 0) gr += hx[m - 1];                      // node at i-1/2
+            if (i == d.Nx - 1) gr += hx[m];                  // last node reuses rho_i twice
+            if (j > 0) gr += hz[m - d.Px];
+            if (j == d.Nz - 1) gr += hz[m];
+            sR += gr;
+        }
+    const long long q = (long long)pj * d.nx + pi;
+    double K, rho;
+    kr_of(pz, xa[q], xb[q], vp_o, rho_o, K, rho);
+    const double vp = sqrt(K / rho), Ko = rho_o * vp_o * vp_o, Io = rho_o * vp_o;
+    const long long P = (long long)d.nx * d.nz;
+    // (A) vp-rho: K = rho vp^2
+    grads[0 * P + q] = vp_o * 2.0 * rho * vp * sK;
+    grads[1 * P + q] = rho_o * (sR + vp * vp * sK);
+    // (B) Ip-rho: K = Ip^2 / rho
+    grads[2 * P + q] = Io * 2.0 * vp * sK;
+    grads[3 * P + q] = rho_o * (sR - vp * vp * sK);
+    // (C) vp-Ip: rho = Ip/vp, K = Ip vp
+    grads[4 * P + q] = vp_o * (rho * vp * sK - rho / vp * sR);
+    grads[5 * P + q] = Io * (vp * sK + sR / vp);
+    // (D) K-rho
+    grads[6 * P + q] = Ko * sK;
+    grads[7 * P + q] = rho_o * sR;
+    // (E) 1/K-1/rho: K = K_o/(1+a), rho = rho_o/(1+b)
+    grads[8 * P + q] = -K * K / Ko * sK;
+    grads[9 * P + q] = -rho * rho / rho_o * sR;
+}
+
+}  // namespace fwi

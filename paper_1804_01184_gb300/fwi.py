@@ -1,0 +1,203 @@
+"""Thin Python binding of libfwi.so (C ABI in include/fwi.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+PyTorch supplies device memory (inputs, outputs and the scratch workspace) and streams.
+The functions carry the C names: ``fwi_model``, ``fwi_born``, ``fwi_adjoint``,
+``fwi_gradient``, ``fwi_workspace_bytes``, ``fwi_status``.
+
+There is no fallback: if libfwi.so has not been built (``paper_1804_01184_gb300.build``)
+or no CUDA device is present, these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+VP_RHO, IP_RHO, VP_IP, K_RHO, INVK_INVRHO = range(5)
+OP_MODEL, OP_BORN, OP_ADJOINT, OP_GRADIENT = range(4)
+ERRORS = {0: "FWI_OK", -1: "FWI_EINVAL", -2: "FWI_ECFL", -3: "FWI_ENOMEM", -4: "FWI_ETIMEOUT", -5: "FWI_ECUDA"}
+
+
+class FwiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    """Mirror of ``fwi_grid``."""
+
+    _fields_ = [
+        ("nx", C.c_int), ("nz", C.c_int), ("sponge", C.c_int), ("order", C.c_int), ("nt", C.c_int),
+        ("dx", C.c_double), ("dt", C.c_double), ("vp_o", C.c_double), ("rho_o", C.c_double),
+        ("sponge_v", C.c_double), ("sponge_R", C.c_double),
+    ]
+
+
+class _Sources(C.Structure):
+    _fields_ = [("ns", C.c_int), ("xy", C.c_void_p), ("wavelet", C.c_void_p)]
+
+
+class _Receivers(C.Structure):
+    _fields_ = [("nr", C.c_int), ("xy", C.c_void_p)]
+
+
+def make_grid(nx, nz, dx, dt, nt, order=8, sponge=40, vp_o=2000.0, rho_o=2000.0, sponge_v=None,
+              sponge_R=1e-3) -> Grid:
+    return Grid(int(nx), int(nz), int(sponge), int(order), int(nt), float(dx), float(dt), float(vp_o),
+                float(rho_o), float(vp_o if sponge_v is None else sponge_v), float(sponge_R))
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libfwi.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfwi.so is not built ({path}); run paper_1804_01184_gb300.build.build()")
+            L = C.CDLL(path)
+            gp, vp, dp = C.POINTER(Grid), C.c_void_p, C.c_void_p
+            sp, rp = C.POINTER(_Sources), C.POINTER(_Receivers)
+            L.fwi_workspace_bytes.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_size_t]
+            L.fwi_workspace_bytes.restype = C.c_size_t
+            L.fwi_model.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp, C.c_size_t, vp]
+            L.fwi_born.argtypes = [gp, C.c_int, vp, vp, vp, vp, sp, rp, vp, vp, C.c_size_t, vp]
+            L.fwi_adjoint.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, vp, C.c_size_t, vp]
+            L.fwi_gradient.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, dp, vp, C.c_size_t, vp]
+            L.fwi_status.argtypes = [vp, vp]
+            L.fwi_last_error.restype = C.c_char_p
+            L.fwi_launch_count.restype = C.c_longlong
+            _lib = L
+    return _lib
+
+
+def _raise(rc):
+    if rc != 0:
+        raise FwiError(rc, lib().fwi_last_error().decode())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev(t, dtype=torch.float32):
+    """Contiguous CUDA tensor of dtype (copies host arrays / numpy to the current device)."""
+    if not torch.is_tensor(t):
+        t = torch.as_tensor(t)
+    if not t.is_cuda:
+        t = t.to("cuda", non_blocking=False)
+    return t.to(dtype).contiguous()
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def fwi_workspace_bytes(grid: Grid, ns: int, nr: int, op: int, budget_bytes: int = 0) -> int:
+    n = lib().fwi_workspace_bytes(C.byref(grid), int(ns), int(nr), int(op), int(budget_bytes))
+    if n == 0:
+        raise FwiError(-1, "invalid grid or sizes")
+    return int(n)
+
+
+def default_budget(device=None) -> int:
+    """Workspace budget: 80 % of the free device memory."""
+    free, _ = torch.cuda.mem_get_info(device)
+    return int(free * 0.8)
+
+
+def workspace(grid: Grid, ns: int, nr: int, op: int, budget_bytes: int | None = None) -> torch.Tensor:
+    """A device buffer of the bytes the library plans for `op` within `budget_bytes`."""
+    budget = default_budget() if budget_bytes is None else int(budget_bytes)
+    n = fwi_workspace_bytes(grid, ns, nr, op, budget)
+    return torch.empty(n, dtype=torch.uint8, device="cuda")
+
+
+def fwi_status(work: torch.Tensor, stream=None):
+    _raise(lib().fwi_status(_ptr(work), _stream(stream)))
+
+
+def launch_count() -> int:
+    return int(lib().fwi_launch_count())
+
+
+def _acq(src_xy, wavelet, rec_xy):
+    s, w, r = _dev(src_xy).reshape(-1, 2), _dev(wavelet).reshape(-1), _dev(rec_xy).reshape(-1, 2)
+    return (s, w, r), _Sources(s.shape[0], s.data_ptr(), w.data_ptr()), _Receivers(r.shape[0], r.data_ptr())
+
+
+def fwi_model(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, traces=None, work=None,
+              stream=None, check=True) -> torch.Tensor:
+    """Forward traces [ns][nr][nt] float32 (see fwi_model in include/fwi.h)."""
+    a, b = _dev(xi_a), _dev(xi_b)
+    keep, S, R = _acq(src_xy, wavelet, rec_xy)
+    if traces is None:
+        traces = torch.empty((S.ns, R.nr, grid.nt), dtype=torch.float32, device="cuda")
+    if work is None:
+        work = workspace(grid, S.ns, R.nr, OP_MODEL)
+    _raise(lib().fwi_model(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(traces),
+                           _ptr(work), work.numel(), _stream(stream)))
+    if check:
+        fwi_status(work, stream)
+    return traces
+
+
+def fwi_born(grid: Grid, pz: int, xi_a, xi_b, dxi_a, dxi_b, src_xy, wavelet, rec_xy, dtraces=None,
+             work=None, stream=None, check=True) -> torch.Tensor:
+    """Born traces [ns][nr][nt] float32 for the contrast perturbation (dxi_a, dxi_b)."""
+    a, b, da, db = _dev(xi_a), _dev(xi_b), _dev(dxi_a), _dev(dxi_b)
+    keep, S, R = _acq(src_xy, wavelet, rec_xy)
+    if dtraces is None:
+        dtraces = torch.empty((S.ns, R.nr, grid.nt), dtype=torch.float32, device="cuda")
+    if work is None:
+        work = workspace(grid, S.ns, R.nr, OP_BORN)
+    _raise(lib().fwi_born(C.byref(grid), int(pz), _ptr(a), _ptr(b), _ptr(da), _ptr(db), C.byref(S),
+                          C.byref(R), _ptr(dtraces), _ptr(work), work.numel(), _stream(stream)))
+    if check:
+        fwi_status(work, stream)
+    return dtraces
+
+
+def fwi_adjoint(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, residual, grads=None, work=None,
+                stream=None, check=True) -> torch.Tensor:
+    """Gradient of sum(residual * traces) for all five parameterizations: [5][2][nz][nx] float64."""
+    a, b, res = _dev(xi_a), _dev(xi_b), _dev(residual)
+    keep, S, R = _acq(src_xy, wavelet, rec_xy)
+    if grads is None:
+        grads = torch.empty((5, 2, grid.nz, grid.nx), dtype=torch.float64, device="cuda")
+    if work is None:
+        work = workspace(grid, S.ns, R.nr, OP_ADJOINT)
+    _raise(lib().fwi_adjoint(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(res),
+                             _ptr(grads), _ptr(work), work.numel(), _stream(stream)))
+    if check:
+        fwi_status(work, stream)
+    return grads
+
+
+def fwi_gradient(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, data, misfit=None, grads=None,
+                 work=None, stream=None, check=True):
+    """Misfit (device float64 scalar tensor) and gradients [5][2][nz][nx] float64."""
+    a, b, d = _dev(xi_a), _dev(xi_b), _dev(data)
+    keep, S, R = _acq(src_xy, wavelet, rec_xy)
+    if grads is None:
+        grads = torch.empty((5, 2, grid.nz, grid.nx), dtype=torch.float64, device="cuda")
+    if misfit is None:
+        misfit = torch.empty((), dtype=torch.float64, device="cuda")
+    if work is None:
+        work = workspace(grid, S.ns, R.nr, OP_GRADIENT)
+    _raise(lib().fwi_gradient(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(d),
+                              _ptr(misfit), _ptr(grads), _ptr(work), work.numel(), _stream(stream)))
+    if check:
+        fwi_status(work, stream)
+    return misfit, grads

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (from the accuracy targets of the method's FP32 path): relative L2 <= 1e-4 on
+traces, <= 1e-3 on every gradient field.  Sizes span several 32 x 32 tiles with a ragged
+tail; the full-size cases use the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_01184_gb300 import inputs as I
+from tests._common import GRAD_TOL, TRACE_TOL, gpu_grid, oracle_grid, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_01184_gb300 import build, fwi
+    build.build()
+    return fwi
+
+
+def run_model(F, w, a=None, b=None, **kw):
+    a = w.xi_a if a is None else a
+    b = w.xi_b if b is None else b
+    return F.fwi_model(gpu_grid(w), w.pz, torch.from_numpy(a), torch.from_numpy(b), torch.from_numpy(w.src_xy),
+                       torch.from_numpy(w.wavelet), torch.from_numpy(w.rec_xy), **kw).cpu().numpy()
+
+
+CASES = [
+    dict(seed=11, nx=75, nz=53, nt=300, order=8, sponge=10, ns=3, nr=9, pz=I.PZ_VP_RHO),
+    dict(seed=12, nx=61, nz=70, nt=250, order=4, sponge=7, ns=2, nr=5, pz=I.PZ_IP_RHO),
+    dict(seed=13, nx=40, nz=33, nt=200, order=8, sponge=0, ns=2, nr=4, pz=I.PZ_VP_IP),
+    dict(seed=14, nx=66, nz=66, nt=260, order=8, sponge=12, ns=4, nr=6, pz=I.PZ_INVK_INVRHO),
+    dict(seed=15, nx=50, nz=45, nt=220, order=4, sponge=5, ns=1, nr=3, pz=I.PZ_K_RHO),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"s{c['seed']}")
+def test_model_parity(F, case):
+    w = I.small_case(**case)
+    tr = run_model(F, w)
+    ref = oracle.model(oracle_grid(w), w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    assert rel_l2(tr, ref) <= TRACE_TOL
+    for s in range(w.ns):   # every shot on its own
+        assert rel_l2(tr[s], ref[s]) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"s{c['seed']}")
+def test_born_parity(F, case):
+    w = I.small_case(**case)
+    da = I.random_like(w.xi_a.shape, 40, 0.05)
+    db = I.random_like(w.xi_a.shape, 41, 0.05)
+    g = gpu_grid(w)
+    dtr = F.fwi_born(g, w.pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy).cpu().numpy()
+    ref = oracle.born(oracle_grid(w), w.pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy)
+    assert rel_l2(dtr, ref) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"s{c['seed']}")
+def test_gradient_parity(F, case):
+    w = I.small_case(**case)
+    og = oracle_grid(w)
+    data = oracle.model(og, w.pz, w.xi_a * 1.4, w.xi_b * 0.6, w.src_xy, w.wavelet, w.rec_xy).astype(np.float32)
+    a0, b0 = (w.xi_a * 0.5).astype(np.float32), (w.xi_b * 0.5).astype(np.float32)
+    J_ref, G_ref = oracle.gradient(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
+    J, G = F.fwi_gradient(gpu_grid(w), w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
+    assert abs(J.item() - J_ref) <= TRACE_TOL * J_ref
+    G = G.cpu().numpy()
+    for pz in range(5):
+        for k in range(2):
+            assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL, (pz, k, rel_l2(G[pz, k], G_ref[pz, k]))
+
+
+def test_adjoint_parity_random_residual(F):
+    w = I.small_case(seed=21, nx=70, nz=58, nt=240, order=8, sponge=9, ns=3, nr=8, pz=I.PZ_VP_RHO)
+    res = I.random_like((w.ns, w.nr, w.nt), 5, 100.0)
+    G = F.fwi_adjoint(gpu_grid(w), w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, res).cpu().numpy()
+    G_ref = oracle.adjoint(oracle_grid(w), w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, res)
+    for pz in range(5):
+        for k in range(2):
+            assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("pz", range(5))
+def test_dot_product_gpu(F, pz):
+    """<born(dm), y> = <dm, adjoint(y)> in FP32 on the GPU."""
+    w = I.small_case(seed=30 + pz, nx=64, nz=48, nt=200, order=8, sponge=8, ns=2, nr=6, pz=pz)
+    g = gpu_grid(w)
+    da, db = I.random_like(w.xi_a.shape, 50, 0.05), I.random_like(w.xi_a.shape, 51, 0.05)
+    y = I.random_like((w.ns, w.nr, w.nt), 52, 1.0)
+    Fx = F.fwi_born(g, pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy).cpu().numpy().astype(np.float64)
+    G = F.fwi_adjoint(g, pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, y).cpu().numpy()
+    lhs = np.sum(Fx * y)
+    rhs = np.sum(G[pz, 0] * da) + np.sum(G[pz, 1] * db)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_checkpointing_and_shot_groups_match(F):
+    """Plans with recomputation from checkpoints and with several shot groups give the
+    gradient of the whole-history single-group plan."""
+    w = I.small_case(seed=41, nx=60, nz=50, nt=300, order=8, sponge=8, ns=5, nr=6, pz=I.PZ_K_RHO)
+    g = gpu_grid(w)
+    data = run_model(F, w, w.xi_a * 1.3, w.xi_b * 0.8)
+    a0, b0 = w.xi_a * 0.5, w.xi_b * 0.5
+    full = F.workspace(g, w.ns, w.nr, F.OP_GRADIENT, 1 << 40)
+    J0, G0 = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data, work=full)
+    minimum = F.fwi_workspace_bytes(g, w.ns, w.nr, F.OP_GRADIENT, 0)
+    for budget in (minimum, int(minimum * 1.6), int(full.numel() * 0.5)):
+        work = F.workspace(g, w.ns, w.nr, F.OP_GRADIENT, budget)
+        assert work.numel() <= max(budget, minimum)
+        J1, G1 = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data, work=work)
+        assert abs(J1.item() - J0.item()) <= 1e-12 * J0.item()
+        assert rel_l2(G1.cpu().numpy(), G0.cpu().numpy()) <= 1e-6
+
+
+def test_model_shot_groups_bitwise(F):
+    w = I.small_case(seed=42, nx=50, nz=40, nt=150, order=8, sponge=6, ns=5, nr=4)
+    g = gpu_grid(w)
+    t_full = run_model(F, w)
+    mn = F.fwi_workspace_bytes(g, w.ns, w.nr, F.OP_MODEL, 0)
+    t_one = run_model(F, w, work=F.workspace(g, w.ns, w.nr, F.OP_MODEL, mn))
+    np.testing.assert_array_equal(t_full, t_one)
+    # each shot alone equals the same shot in the batch
+    for s in range(w.ns):
+        np.testing.assert_array_equal(run_model(F, w.subset([s]))[0], t_full[s])
+
+
+# -------------------------------------------------------------------- full-size workloads
+
+def test_config_point_full(F):
+    """201 x 201 + 40-cell sponge, 4th order, 800 steps, 8 sources / 64 receivers: traces and
+    K-rho gradient (the record at 800 steps ends before the scattered arrivals; the gradient
+    is also checked at 1400 steps, where they are inside the record)."""
+    for nt in (800, 1400):
+        w = I.config_point(nt)
+        og = oracle_grid(w)
+        tr = run_model(F, w)
+        ref = oracle.model(og, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+        assert rel_l2(tr, ref) <= TRACE_TOL
+        if nt == 800:   # residual would be FP32 noise only: nothing scattered has arrived
+            continue
+        a0, b0 = w.background()
+        data = ref.astype(np.float32)
+        J_ref, G_ref = oracle.gradient(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
+        J, G = F.fwi_gradient(gpu_grid(w), w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
+        assert abs(J.item() - J_ref) <= 1e-3 * J_ref
+        G = G.cpu().numpy()
+        for pz in range(5):
+            for k in range(2):
+                assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL, (nt, pz, k)
+
+
+def test_config_gaussian_full_traces_sampled(F):
+    """601 x 601, 8th order, 3000 steps, 64 sources / 256 receivers (the benchmark's launch
+    configuration): all 64 shots on the GPU, shots 0 and 37 recomputed by the oracle."""
+    w = I.config_gaussian(0.3, "vp")
+    tr = run_model(F, w)
+    assert tr.shape == (64, 256, 3000) and np.all(np.isfinite(tr))
+    og = oracle_grid(w)
+    for s in (0, 37):
+        sub = w.subset([s])
+        ref = oracle.model(og, w.pz, w.xi_a, w.xi_b, sub.src_xy, w.wavelet, w.rec_xy)[0]
+        assert rel_l2(tr[s], ref) <= TRACE_TOL, s
+
+
+def test_config_gaussian_full_adjoint_sampled(F):
+    """Full 681 x 681 computational grid and 8th order; a random residual on 2 shots over 400
+    steps (the oracle keeps the whole FP64 history in host memory)."""
+    w = I.config_gaussian(0.3, "rho", nt=400)
+    sub = w.subset([5, 50])
+    res = I.random_like((2, w.nr, w.nt), 77, 1e3)
+    G = F.fwi_adjoint(gpu_grid(w), w.pz, w.xi_a, w.xi_b, sub.src_xy, w.wavelet, w.rec_xy, res).cpu().numpy()
+    G_ref = oracle.adjoint(oracle_grid(w), w.pz, w.xi_a, w.xi_b, sub.src_xy, w.wavelet, w.rec_xy, res)
+    for pz in range(5):
+        for k in range(2):
+            assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL
+
+
+# ---------------------------------------------------------------------------- edge cases
+
+def test_empty_shots_and_receivers(F):
+    w = I.small_case(seed=50, nx=30, nz=30, nt=50, ns=2, nr=3)
+    g = gpu_grid(w)
+    none_s = np.zeros((0, 2), np.float32)
+    tr = F.fwi_model(g, w.pz, w.xi_a, w.xi_b, none_s, w.wavelet, w.rec_xy)
+    assert tr.shape == (0, w.nr, w.nt)
+    tr = F.fwi_model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, none_s)
+    assert tr.shape == (w.ns, 0, w.nt)
+    J, G = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, none_s, w.wavelet, w.rec_xy, np.zeros((0, w.nr, w.nt), np.float32))
+    assert J.item() == 0.0 and torch.all(G == 0)
+    J, G = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, none_s, np.zeros((w.ns, 0, w.nt), np.float32))
+    assert J.item() == 0.0 and torch.all(G == 0)
+
+
+def test_zero_residual_gives_zero_gradient(F):
+    w = I.small_case(seed=51, nx=40, nz=40, nt=120, ns=2, nr=5)
+    data = run_model(F, w)
+    J, G = F.fwi_gradient(gpu_grid(w), w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, data)
+    assert J.item() == 0.0 and torch.all(G == 0)
+
+
+def test_errors_reported(F):
+    w = I.small_case(seed=52, nx=30, nz=30, nt=40, ns=1, nr=2)
+    g = gpu_grid(w)
+    bad = w.xi_a.copy()
+    bad[3, 4] = -1.5
+    with pytest.raises(F.FwiError) as e:
+        F.fwi_model(g, w.pz, bad, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    assert e.value.code == -1
+    with pytest.raises(F.FwiError) as e:     # dt far above the stability limit
+        F.fwi_model(gpu_grid(w, dt=5e-3), w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet[:40], w.rec_xy)
+    assert e.value.code == -2
+    with pytest.raises(F.FwiError) as e:     # receiver outside the physical grid
+        F.fwi_model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, np.array([[1e4, 0.0]], np.float32))
+    assert e.value.code == -1
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(F.FwiError) as e:
+        F.fwi_model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, work=small)
+    assert e.value.code == -3
+    # the context is still usable
+    run_model(F, w)
