@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="gradient workspace budget (0: 80%% of free device memory)")
     return ap.parse_args()
 
 
@@ -209,7 +211,8 @@ def main():
     dtr = torch.empty_like(data)
     grads = torch.empty((5, 2, w0.nz, w0.nx), dtype=torch.float64, device=dev)
     misfit = torch.empty((), dtype=torch.float64, device=dev)
-    ws_grad = fwi.workspace(g, ns, nr, fwi.OP_GRADIENT)
+    ws_grad = fwi.workspace(g, ns, nr, fwi.OP_GRADIENT,
+                            int(args.budget_gb * 2**30) if args.budget_gb > 0 else None)
     stream = torch.cuda.current_stream(dev)
     launches = [0]
 

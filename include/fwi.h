@@ -137,6 +137,12 @@ const char *fwi_last_error(void);
 /* Kernels launched by the last operation on this thread (for launch accounting). */
 long long fwi_launch_count(void);
 
+/* Launch-shape tuning (no counterpart in the paper: the autotuner's hook).  Sets, for plans
+ * made afterwards by any thread, the strip height of the streaming kernels (multiple of 8;
+ * 0 = built-in default) and the kernel variant (0 = full register budget, 1 = at most 128
+ * registers per thread).  Results are identical for every setting; only speed changes. */
+int fwi_set_tile(int tz, int variant);
+
 /* Per-launch timing (no counterpart in the paper: measurement support).  While enabled,
  * every kernel launch of the library is bracketed by a CUDA event pair recorded on the
  * launching stream.  fwi_profile_report() waits for those events, writes one line per kernel

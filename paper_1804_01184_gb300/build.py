@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfwi.so")
 SOURCES = [os.path.join(CSRC, "fwi_api.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "fwi_kernels.cuh"), os.path.join(ROOT, "include", "fwi.h")]
+DEPS = SOURCES + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".cu", ".h"))) + \
+    [os.path.join(ROOT, "include", "fwi.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -16,6 +16,8 @@
 
 #include "../../include/fwi.h"
 #include "fwi_kernels.cuh"
+#include "fwi_stream.cuh"
+#include "fwi_warp.cuh"
 
 namespace {
 
@@ -74,6 +76,10 @@ struct Profiler {
 };
 Profiler g_prof;
 
+// Launch-shape overrides set by fwi_set_tile (0: built-in defaults); read when a plan is made.
+int g_tile_tz = 0;
+int g_tile_variant = 0;
+
 constexpr size_t ALIGN = 256;
 constexpr int RED_BLOCKS = 264;   // misfit partial sums per shot group
 
@@ -87,19 +93,26 @@ struct Plan {
     int C = 0;        // steps per snapshot segment (== nt: whole history kept)
     int nseg = 1;     // segments
     int ngroups = 0;
+    int NT = 0;       // threads of a row-streaming CTA (4 columns each)
+    int tz = 0;       // rows per row-streaming CTA / warp strip
+    int variant = 0;  // kernel variant (register budget) chosen by the tuner
     // byte offsets into the workspace
     size_t status = 0, K = 0, bx = 0, bz = 0, ax = 0, axh = 0, az = 0, azh = 0;
     size_t sidx = 0, sw = 0, ridx = 0, rw = 0;
-    size_t p = 0, vx = 0, vz = 0;
-    size_t dK = 0, dbx = 0, dbz = 0, dp = 0, dvx = 0, dvz = 0;
-    size_t ap = 0, avx = 0, avz = 0, accK = 0, accBx = 0, accBz = 0, snap = 0, ckpt = 0;
+    size_t p[2] = {0, 0}, vx[2] = {0, 0}, vz[2] = {0, 0};          // ping-pong state
+    size_t dK = 0, dbx = 0, dbz = 0, dp[2] = {0, 0}, dvx[2] = {0, 0}, dvz[2] = {0, 0};
+    size_t ap[2] = {0, 0}, avx[2] = {0, 0}, avz[2] = {0, 0};
+    size_t accK = 0, accBx = 0, accBz = 0, snap = 0, ckpt = 0;
     size_t gK = 0, hx = 0, hz = 0, traces = 0, partial = 0;
     size_t total = 0;
 };
 
+constexpr int MAX_NX = 1536;   // computational columns: one streaming CTA of <= 384 threads spans a row
+
 bool grid_ok(const fwi_grid *g)
 {
     return g && g->nx >= 2 && g->nz >= 2 && g->sponge >= 0 && (g->order == 4 || g->order == 8) &&
+           g->nx + 2 * g->sponge <= MAX_NX &&
            g->nt >= 1 && g->dx > 0 && g->dt > 0 && g->vp_o > 0 && g->rho_o > 0 &&
            std::isfinite(g->dx) && std::isfinite(g->dt);
 }
@@ -120,6 +133,9 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
         P.st.c[k] = (float)(c * g->dt / g->dx);
     }
     P.ns = ns; P.nr = nr; P.nt = g->nt;
+    P.NT = (int)up((size_t)(d.Nx + 3) / 4, 32);
+    P.tz = g_tile_tz > 0 ? g_tile_tz : 64;
+    P.variant = g_tile_variant;
     P.B = std::max(1, std::min(B, std::max(ns, 1)));
     P.C = std::max(1, std::min(C, g->nt));
     P.nseg = (g->nt + P.C - 1) / P.C;
@@ -136,13 +152,13 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
     P.sw = take(4 * (size_t)std::max(ns, 1) * F);
     P.ridx = take(4 * (size_t)std::max(nr, 1) * sizeof(long long));
     P.rw = take(4 * (size_t)std::max(nr, 1) * F);
-    P.p = take(bfield); P.vx = take(bfield); P.vz = take(bfield);
+    for (int b = 0; b < 2; ++b) { P.p[b] = take(bfield); P.vx[b] = take(bfield); P.vz[b] = take(bfield); }
     if (op == FWI_OP_BORN) {
         P.dK = take(field); P.dbx = take(field); P.dbz = take(field);
-        P.dp = take(bfield); P.dvx = take(bfield); P.dvz = take(bfield);
+        for (int b = 0; b < 2; ++b) { P.dp[b] = take(bfield); P.dvx[b] = take(bfield); P.dvz[b] = take(bfield); }
     }
     if (op == FWI_OP_ADJOINT || op == FWI_OP_GRADIENT) {
-        P.ap = take(bfield); P.avx = take(bfield); P.avz = take(bfield);
+        for (int b = 0; b < 2; ++b) { P.ap[b] = take(bfield); P.avx[b] = take(bfield); P.avz[b] = take(bfield); }
         P.accK = take(bfield); P.accBx = take(bfield); P.accBz = take(bfield);
         P.snap = take((size_t)(P.C + 1) * bfield);
         if (P.nseg > 1) P.ckpt = take((size_t)P.nseg * 3 * bfield);
@@ -202,7 +218,9 @@ T *at(void *work, size_t off) { return reinterpret_cast<T *>(static_cast<char *>
 int check_common(const fwi_grid *g, const float *xa, const float *xb, const fwi_sources *src,
                  const fwi_receivers *rec, void *work, size_t work_bytes)
 {
-    if (!grid_ok(g)) return fail(FWI_EINVAL, "invalid grid (nx, nz >= 2, order 4 or 8, nt >= 1, dx, dt, vp_o, rho_o > 0)");
+    if (!grid_ok(g))
+        return fail(FWI_EINVAL, "invalid grid (nx, nz >= 2, nx + 2 sponge <= %d, order 4 or 8, nt >= 1, "
+                                "dx, dt, vp_o, rho_o > 0)", MAX_NX);
     if (!xa || !xb) return fail(FWI_EINVAL, "null contrast pointer");
     if (!src || !rec || src->ns < 0 || rec->nr < 0) return fail(FWI_EINVAL, "invalid sources/receivers");
     if (src->ns > 0 && (!src->xy || !src->wavelet)) return fail(FWI_EINVAL, "null source arrays");
@@ -233,11 +251,6 @@ int cuda_fail(cudaError_t e, const char *what)
         ++g_launches;                                              \
     } while (0)
 
-dim3 tiles(const fwi::Dims &d, int shots)
-{
-    return dim3((d.Nx + fwi::TX - 1) / fwi::TX, (d.Nz + fwi::TZ - 1) / fwi::TZ, shots);
-}
-const dim3 kBlock(fwi::TX, fwi::NTY);
 
 // Model, sponge tables and acquisition geometry (S1, S2).
 int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float *xb,
@@ -267,40 +280,62 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
     return FWI_OK;
 }
 
+// Row-streaming launch shape: grid (strips, shots), block NT, dynamic shared memory for
+// (rings + 2) shared rows.
+dim3 strips(const Plan &P, int shots) { return dim3((P.d.Nz + P.tz - 1) / P.tz, shots); }
+size_t stream_smem(const Plan &P, int rows) { return (size_t)rows * (4 * P.NT + 2 * fwi::SHALO) * sizeof(float); }
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Warp-strip launch shape: one warp per (128-column strip, tz-row strip, shot), 2 warps a block.
+dim3 warp_grid(const Plan &P, int shots)
+{
+    const long long warps = (long long)((P.d.Nx + fwi::WS - 1) / fwi::WS) * ((P.d.Nz + P.tz - 1) / P.tz) * shots;
+    return dim3((unsigned)((warps + 1) / 2));
+}
+
+fwi::Model model_of(const Plan &P, void *work)
+{
+    return fwi::Model{at<float>(work, P.K), at<float>(work, P.bx), at<float>(work, P.bz), at<float>(work, P.ax),
+                      at<float>(work, P.axh), at<float>(work, P.az), at<float>(work, P.azh)};
+}
+
 struct Fwd {
     const Plan &P;
     void *work;
     cudaStream_t st;
     const float *wav;
 
-    // one forward step n for the group's shots [s0, s0 + bg)
-    void step(int n, int s0, int bg, float *snap) const
+    // one forward step n for the group's shots [s0, s0 + bg): p^n in p0 -> p^{n+1} in p1,
+    // velocities ping-pong on the parity of n
+    void step(int n, int s0, int bg, const float *p0, float *p1) const
     {
         const fwi::Dims &d = P.d;
-        float *p = at<float>(work, P.p), *vx = at<float>(work, P.vx), *vz = at<float>(work, P.vz);
-        const float *K = at<float>(work, P.K), *bx = at<float>(work, P.bx), *bz = at<float>(work, P.bz);
-        const float *ax = at<float>(work, P.ax), *axh = at<float>(work, P.axh);
-        const float *az = at<float>(work, P.az), *azh = at<float>(work, P.azh);
-        const long long *sidx = at<long long>(work, P.sidx) + 4LL * s0;
-        const float *sw = at<float>(work, P.sw) + 4LL * s0;
+        const fwi::Source src{at<long long>(work, P.sidx) + 4LL * s0, at<float>(work, P.sw) + 4LL * s0, wav};
+        const float *vx0 = at<float>(work, P.vx[n & 1]), *vz0 = at<float>(work, P.vz[n & 1]);
+        float *vx1 = at<float>(work, P.vx[(n + 1) & 1]), *vz1 = at<float>(work, P.vz[(n + 1) & 1]);
+        const dim3 grid = warp_grid(P, bg);
+        const fwi::Model mo = model_of(P, work);
         if (P.M == 2) {
-            LAUNCH(fwi::k_fwd_v<2>, tiles(d, bg), kBlock, 0, st, p, vx, vz, bx, bz, ax, axh, az, azh, d, P.st);
-            if (snap)
-                LAUNCH((fwi::k_fwd_p<2, true>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+            if (P.variant == 1)
+                LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
             else
-                LAUNCH((fwi::k_fwd_p<2, false>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+                LAUNCH((fwi::k_fwd_warp<2, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
         } else {
-            LAUNCH(fwi::k_fwd_v<4>, tiles(d, bg), kBlock, 0, st, p, vx, vz, bx, bz, ax, axh, az, azh, d, P.st);
-            if (snap)
-                LAUNCH((fwi::k_fwd_p<4, true>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+            if (P.variant == 1)
+                LAUNCH((fwi::k_fwd_warp<4, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
             else
-                LAUNCH((fwi::k_fwd_p<4, false>), tiles(d, bg), kBlock, 0, st, p, vx, vz, K, ax, az, d, P.st, sidx, sw, wav, n, snap);
+                LAUNCH((fwi::k_fwd_warp<4, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
         }
     }
-    void sample(int n, int bg, int nr, float *traces) const
+    void sample(int n, int bg, int nr, const float *p, float *traces) const
     {
         if (nr == 0) return;
-        LAUNCH(fwi::k_sample, (bg * nr + 127) / 128, 128, 0, st, at<float>(work, P.p), bg, nr, P.nt, n, P.d.Np,
+        LAUNCH(fwi::k_sample, (bg * nr + 127) / 128, 128, 0, st, p, bg, nr, P.nt, n, P.d.Np,
                at<long long>(work, P.ridx), at<float>(work, P.rw), traces);
     }
 };
@@ -322,32 +357,33 @@ int plan_for(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, size_t work_
 }
 
 // Forward over all steps for one group, used by model, adjoint and gradient.
-//   traces: [bg][nr][nt] output or null;  with_hist: keep snapshots / checkpoints for the adjoint.
+//   traces: [bg][nr][nt] output or null.
+//   with_hist: keep the pressure history of the last segment (it is the pressure state of those
+//   steps: p^n lives in snapshot slot n - last0) and checkpoints (p, vx, vz) every C steps.
 int forward_group(const Plan &P, void *work, cudaStream_t st, const float *wav, int s0, int bg,
                   float *traces, bool with_hist)
 {
     const Fwd f{P, work, st, wav};
     const size_t bf = (size_t)bg * P.d.Np * sizeof(float);
-    CK(cudaMemsetAsync(at<char>(work, P.p), 0, bf, st));
-    CK(cudaMemsetAsync(at<char>(work, P.vx), 0, bf, st));
-    CK(cudaMemsetAsync(at<char>(work, P.vz), 0, bf, st));
     const size_t slot = (size_t)P.B * P.d.Np;   // floats between snapshot slots
-    const int last0 = (P.nseg - 1) * P.C;       // first step of the last segment
+    const int last0 = with_hist ? (P.nseg - 1) * P.C : P.nt + 1;
+    float *snap = with_hist ? at<float>(work, P.snap) : nullptr;
+    auto pbuf = [&](int n) -> float * {
+        return n >= last0 ? snap + (size_t)(n - last0) * slot : at<float>(work, P.p[n & 1]);
+    };
+    CK(cudaMemsetAsync(pbuf(0), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.vx[0]), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.vz[0]), 0, bf, st));
     for (int n = 0; n < P.nt; ++n) {
-        float *snap = nullptr;
-        if (with_hist) {
-            if (P.nseg > 1 && n % P.C == 0) {
-                float *ck = at<float>(work, P.ckpt) + (size_t)(n / P.C) * 3 * slot;
-                CK(cudaMemcpyAsync(ck, at<float>(work, P.p), bf, cudaMemcpyDeviceToDevice, st));
-                CK(cudaMemcpyAsync(ck + slot, at<float>(work, P.vx), bf, cudaMemcpyDeviceToDevice, st));
-                CK(cudaMemcpyAsync(ck + 2 * slot, at<float>(work, P.vz), bf, cudaMemcpyDeviceToDevice, st));
-            }
-            if (n == last0)
-                CK(cudaMemcpyAsync(at<float>(work, P.snap), at<float>(work, P.p), bf, cudaMemcpyDeviceToDevice, st));
-            if (n >= last0) snap = at<float>(work, P.snap) + (size_t)(n + 1 - last0) * slot;
+        if (with_hist && P.nseg > 1 && n % P.C == 0) {
+            float *ck = at<float>(work, P.ckpt) + (size_t)(n / P.C) * 3 * slot;
+            CK(cudaMemcpyAsync(ck, pbuf(n), bf, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(ck + slot, at<float>(work, P.vx[n & 1]), bf, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(ck + 2 * slot, at<float>(work, P.vz[n & 1]), bf, cudaMemcpyDeviceToDevice, st));
         }
-        f.step(n, s0, bg, snap);
-        if (traces) f.sample(n, bg, P.nr, traces);
+        float *p1 = pbuf(n + 1);
+        f.step(n, s0, bg, pbuf(n), p1);
+        if (traces) f.sample(n, bg, P.nr, p1, traces);
     }
     return FWI_OK;
 }
@@ -361,38 +397,42 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
     const Fwd f{P, work, st, wav};
     const size_t bf = (size_t)bg * d.Np * sizeof(float);
     const size_t slot = (size_t)P.B * d.Np;
-    float *ap = at<float>(work, P.ap), *avx = at<float>(work, P.avx), *avz = at<float>(work, P.avz);
-    CK(cudaMemsetAsync(ap, 0, bf, st));
-    CK(cudaMemsetAsync(avx, 0, bf, st));
-    CK(cudaMemsetAsync(avz, 0, bf, st));
-    const float *K = at<float>(work, P.K), *bx = at<float>(work, P.bx), *bz = at<float>(work, P.bz);
-    const float *ax = at<float>(work, P.ax), *axh = at<float>(work, P.axh);
-    const float *az = at<float>(work, P.az), *azh = at<float>(work, P.azh);
+    const int first = P.nt & 1;   // buffers holding pbar^{nt}, vbar^{nt-1/2} = 0
+    CK(cudaMemsetAsync(at<char>(work, P.ap[first]), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.avx[first]), 0, bf, st));
+    CK(cudaMemsetAsync(at<char>(work, P.avz[first]), 0, bf, st));
+    const fwi::Model mo = model_of(P, work);
     float *aK = at<float>(work, P.accK), *aBx = at<float>(work, P.accBx), *aBz = at<float>(work, P.accBz);
     float *snap = at<float>(work, P.snap);
     for (int k = P.nseg - 1; k >= 0; --k) {
         const int n0 = k * P.C, n1 = std::min(n0 + P.C, P.nt);
         if (k < P.nseg - 1) {   // recompute the segment from its checkpoint
             const float *ck = at<float>(work, P.ckpt) + (size_t)k * 3 * slot;
-            CK(cudaMemcpyAsync(at<float>(work, P.p), ck, bf, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(at<float>(work, P.vx), ck + slot, bf, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(at<float>(work, P.vz), ck + 2 * slot, bf, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(snap, ck, bf, cudaMemcpyDeviceToDevice, st));
-            for (int n = n0; n < n1; ++n) f.step(n, s0, bg, snap + (size_t)(n + 1 - n0) * slot);
+            CK(cudaMemcpyAsync(at<float>(work, P.vx[n0 & 1]), ck + slot, bf, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(at<float>(work, P.vz[n0 & 1]), ck + 2 * slot, bf, cudaMemcpyDeviceToDevice, st));
+            for (int n = n0; n < n1; ++n)
+                f.step(n, s0, bg, snap + (size_t)(n - n0) * slot, snap + (size_t)(n + 1 - n0) * slot);
         }
         for (int n = n1 - 1; n >= n0; --n) {
+            const int i = (n + 1) & 1, o = n & 1;
+            float *ap0 = at<float>(work, P.ap[i]);
             if (P.nr > 0)
-                LAUNCH(fwi::k_adj_inject, (bg * P.nr + 127) / 128, 128, 0, st, ap, bg, P.nr, P.nt, n, d.Np,
+                LAUNCH(fwi::k_adj_inject, (bg * P.nr + 127) / 128, 128, 0, st, ap0, bg, P.nr, P.nt, n, d.Np,
                        at<long long>(work, P.ridx), at<float>(work, P.rw), res);
             const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
+            const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
+            float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
             if (P.M == 2) {
-                LAUNCH(fwi::k_adj_v<2>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, K, ax, axh, az, azh, pn, pn1,
-                       aK, aBx, aBz, d, P.st);
-                LAUNCH(fwi::k_adj_p<2>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, bx, bz, ax, az, d, P.st);
+                const size_t sm = stream_smem(P, 4 * 2 + 2);
+                allow_smem(fwi::k_adj_stream<2>, sm);
+                LAUNCH(fwi::k_adj_stream<2>, strips(P, bg), P.NT, sm, st, ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, pn1,
+                       aK, aBx, aBz, d, P.st, P.tz);
             } else {
-                LAUNCH(fwi::k_adj_v<4>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, K, ax, axh, az, azh, pn, pn1,
-                       aK, aBx, aBz, d, P.st);
-                LAUNCH(fwi::k_adj_p<4>, tiles(d, bg), kBlock, 0, st, ap, avx, avz, bx, bz, ax, az, d, P.st);
+                const size_t sm = stream_smem(P, 4 * 4 + 2);
+                allow_smem(fwi::k_adj_stream<4>, sm);
+                LAUNCH(fwi::k_adj_stream<4>, strips(P, bg), P.NT, sm, st, ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, pn1,
+                       aK, aBx, aBz, d, P.st, P.tz);
             }
         }
     }
@@ -510,29 +550,32 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
     dim3 b2(32, 8), g2((d.Px + 31) / 32, (d.Nz + 7) / 8);
     LAUNCH(fwi::k_model_pert, g2, b2, 0, st, xi_a, xi_b, dxi_a, dxi_b, (int)pz, g->vp_o, g->rho_o, d,
            at<float>(work, P.dK), at<float>(work, P.dbx), at<float>(work, P.dbz));
-    float *p = at<float>(work, P.p), *vx = at<float>(work, P.vx), *vz = at<float>(work, P.vz);
-    float *dp = at<float>(work, P.dp), *dvx = at<float>(work, P.dvx), *dvz = at<float>(work, P.dvz);
-    const float *K = at<float>(work, P.K), *bx = at<float>(work, P.bx), *bz = at<float>(work, P.bz);
-    const float *dK = at<float>(work, P.dK), *dbx = at<float>(work, P.dbx), *dbz = at<float>(work, P.dbz);
-    const float *ax = at<float>(work, P.ax), *axh = at<float>(work, P.axh);
-    const float *az = at<float>(work, P.az), *azh = at<float>(work, P.azh);
+    const fwi::Model mo = model_of(P, work);
+    const fwi::Pert pe{at<float>(work, P.dK), at<float>(work, P.dbx), at<float>(work, P.dbz)};
     for (int gi = 0; gi < P.ngroups; ++gi) {
         const int s0 = gi * P.B, bg = std::min(P.B, P.ns - s0);
         const size_t bf = (size_t)bg * d.Np * sizeof(float);
-        for (float *f : {p, vx, vz, dp, dvx, dvz}) CK(cudaMemsetAsync(f, 0, bf, st));
-        const long long *sidx = at<long long>(work, P.sidx) + 4LL * s0;
-        const float *sw = at<float>(work, P.sw) + 4LL * s0;
+        for (size_t off : {P.p[0], P.vx[0], P.vz[0], P.dp[0], P.dvx[0], P.dvz[0]})
+            CK(cudaMemsetAsync(at<char>(work, off), 0, bf, st));
+        const fwi::Source sr{at<long long>(work, P.sidx) + 4LL * s0, at<float>(work, P.sw) + 4LL * s0, src->wavelet};
         float *out = dtraces + (size_t)s0 * P.nr * P.nt;
         for (int n = 0; n < P.nt; ++n) {
+            const int i = n & 1, o = (n + 1) & 1;
+            auto F = [&](const size_t *a) { return at<float>(work, a[i]); };
+            auto G = [&](const size_t *a) { return at<float>(work, a[o]); };
             if (P.M == 2) {
-                LAUNCH(fwi::k_born_v<2>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, bx, bz, dbx, dbz, ax, axh, az, azh, d, P.st);
-                LAUNCH(fwi::k_born_p<2>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, K, dK, ax, az, d, P.st, sidx, sw, src->wavelet, n);
+                const size_t sm = stream_smem(P, 4 * 2 + 4);
+                allow_smem(fwi::k_born_stream<2>, sm);
+                LAUNCH(fwi::k_born_stream<2>, strips(P, bg), P.NT, sm, st, F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx),
+                       F(P.dvz), G(P.p), G(P.vx), G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz);
             } else {
-                LAUNCH(fwi::k_born_v<4>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, bx, bz, dbx, dbz, ax, axh, az, azh, d, P.st);
-                LAUNCH(fwi::k_born_p<4>, tiles(d, bg), kBlock, 0, st, p, vx, vz, dp, dvx, dvz, K, dK, ax, az, d, P.st, sidx, sw, src->wavelet, n);
+                const size_t sm = stream_smem(P, 4 * 4 + 4);
+                allow_smem(fwi::k_born_stream<4>, sm);
+                LAUNCH(fwi::k_born_stream<4>, strips(P, bg), P.NT, sm, st, F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx),
+                       F(P.dvz), G(P.p), G(P.vx), G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz);
             }
             if (P.nr > 0)
-                LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, dp, bg, P.nr, P.nt, n, d.Np,
+                LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, G(P.dp), bg, P.nr, P.nt, n, d.Np,
                        at<long long>(work, P.ridx), at<float>(work, P.rw), out);
         }
     }
@@ -581,10 +624,19 @@ int fwi_status(void *work, void *stream)
     CK(cudaStreamSynchronize(st));
     if (h & fwi::ST_EINVAL) return fail(FWI_EINVAL, "a contrast has 1 + xi <= 0 or a position lies outside the physical grid");
     if (h & fwi::ST_ECFL) return fail(FWI_ECFL, "dt exceeds the stability limit of the stencil for this model");
+    if (h & fwi::ST_ETIMEOUT) return fail(FWI_ETIMEOUT, "a bounded wait for a TMA row copy expired");
     return FWI_OK;
 }
 
 const char *fwi_last_error(void) { return g_err.c_str(); }
+
+int fwi_set_tile(int tz, int variant)
+{
+    if (tz < 0 || tz % 8 || variant < 0 || variant > 1) return fail(FWI_EINVAL, "tile height must be a multiple of 8, variant 0 or 1");
+    g_tile_tz = tz;
+    g_tile_variant = variant;
+    return FWI_OK;
+}
 
 int fwi_profile(int enable)
 {

@@ -19,11 +19,6 @@
 
 namespace fwi {
 
-constexpr int TX = 32;        // tile width (one warp across)
-constexpr int TZ = 32;        // tile height
-constexpr int NTY = 8;        // threads in z per block (block = 32 x 8)
-constexpr int RZ = TZ / NTY;  // rows per thread
-
 struct Dims {
     int Nx, Nz, Px;       // computational grid and row pitch
     int nx, nz, S;        // physical grid and sponge width
@@ -179,109 +174,22 @@ __global__ void k_geometry(const float *__restrict__ xy, int n, Dims d, double d
     idx[4 * k + 3] = cell(d, i0 + 1, j0 + 1);  w[4 * k + 3] = (float)(scale * tx * tz);
 }
 
-// ------------------------------------------------------------- tile loads (shared memory)
+// ------------------------------------------------------------ shared kernel arguments
 
-// Loads rows [z0 + r0, z0 + r0 + H) x cols [x0 + c0, x0 + c0 + W) of field f (one shot)
-// into s[H][W], zero outside the computational grid; optionally multiplied by a
-// per-cell factor fn(i, j, value).
-template <int H, int W, typename F>
-__device__ __forceinline__ void load_tile(float (&s)[H][W], const float *__restrict__ f, const Dims &d,
-                                          int x0, int z0, int c0, int r0, F fn)
-{
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int t = tid; t < H * W; t += TX * NTY) {
-        const int r = t / W, c = t - r * W;
-        const int gz = z0 + r0 + r, gx = x0 + c0 + c;
-        float v = 0.f;
-        if (gz >= 0 && gz < d.Nz && gx >= 0 && gx < d.Nx) v = fn(gx, gz, __ldg(f + cell(d, gx, gz)));
-        s[r][c] = v;
-    }
-}
-
-struct Ident {
-    __device__ __forceinline__ float operator()(int, int, float v) const { return v; }
+struct Model {
+    const float *K, *bx, *bz, *ax, *axh, *az, *azh;
 };
 
-// ------------------------------------------------------------------ forward step (S3)
+struct Source {
+    const long long *idx;   // [shot][4] cell offsets (relative to the shot's field)
+    const float *w;         // [shot][4] dt beta / dx^2
+    const float *wav;       // wavelet, sample n at (n+1/2) dt
+};
 
-// Velocity half step: v^{n+1/2} = d_v (v^{n-1/2} - dt b D+ p^n) for all shots (blockIdx.z).
-template <int M>
-__global__ void __launch_bounds__(TX *NTY) k_fwd_v(const float *__restrict__ p, float *__restrict__ vx,
-                                                  float *__restrict__ vz, const float *__restrict__ bx,
-                                                  const float *__restrict__ bz,
-                                                  const float *__restrict__ ax, const float *__restrict__ axh,
-                                                  const float *__restrict__ az, const float *__restrict__ azh,
-                                                  Dims d, Stencil st)
-{
-    constexpr int H = TZ + 2 * M - 1, W = TX + 2 * M - 1;
-    __shared__ float sp[H][W];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const long long so = (long long)blockIdx.z * d.Np;
-    load_tile(sp, p + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
-    __syncthreads();
-    const int lx = threadIdx.x, gx = x0 + lx;
-    if (gx >= d.Nx) return;
-    const float axv = ax[gx], axhv = axh[gx];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
-        if (gz >= d.Nz) break;
-        float gxp = 0.f, gzp = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            gxp += st.c[k - 1] * (sp[lz + M - 1][lx + M - 1 + k] - sp[lz + M - 1][lx + M - k]);
-            gzp += st.c[k - 1] * (sp[lz + M - 1 + k][lx + M - 1] - sp[lz + M - k][lx + M - 1]);
-        }
-        const long long m = cell(d, gx, gz), o = so + m;
-        vx[o] = axhv * az[gz] * (vx[o] - bx[m] * gxp);
-        vz[o] = axv * azh[gz] * (vz[o] - bz[m] * gzp);
-    }
-}
-
-// Pressure step: p^{n+1} = d_p (p^n - dt K D-.v^{n+1/2}) + dt K w_n beta / dx^2 at the
-// source cells of the shot; optionally stores p^{n+1} as a snapshot.
-template <int M, bool SNAP>
-__global__ void __launch_bounds__(TX *NTY) k_fwd_p(float *__restrict__ p, const float *__restrict__ vx,
-                                                  const float *__restrict__ vz, const float *__restrict__ K,
-                                                  const float *__restrict__ ax, const float *__restrict__ az,
-                                                  Dims d, Stencil st, const long long *__restrict__ sidx,
-                                                  const float *__restrict__ sw, const float *__restrict__ wav,
-                                                  int n, float *__restrict__ snap)
-{
-    __shared__ float sx[TZ][TX + 2 * M - 1];
-    __shared__ float sz[TZ + 2 * M - 1][TX];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, s = blockIdx.z;
-    const long long so = (long long)s * d.Np;
-    load_tile(sx, vx + so, d, x0, z0, -M, 0, Ident());
-    load_tile(sz, vz + so, d, x0, z0, 0, -M, Ident());
-    __syncthreads();
-    const int lx = threadIdx.x, gx = x0 + lx;
-    if (gx >= d.Nx) return;
-    long long si[4];
-    float swv[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) { si[c] = sidx[4 * s + c]; swv[c] = sw[4 * s + c]; }
-    const float axv = ax[gx];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
-        if (gz >= d.Nz) break;
-        float dv = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            dv += st.c[k - 1] * (sx[lz][lx + M + k - 1] - sx[lz][lx + M - k]);
-            dv += st.c[k - 1] * (sz[lz + M + k - 1][lx] - sz[lz + M - k][lx]);
-        }
-        const long long m = cell(d, gx, gz), o = so + m;
-        const float Kv = K[m];
-        float pn = axv * az[gz] * (p[o] - Kv * dv);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (si[c] == m) pn += Kv * __ldg(wav + n) * swv[c];
-        p[o] = pn;
-        if (SNAP) snap[o] = pn;
-    }
-}
+// Born perturbation of the model: dK, dbx, dbz on the padded grid
+struct Pert {
+    const float *dK, *dbx, *dbz;
+};
 
 // trace[s][r][n] = sum_c beta_rc p^{n+1}[cell_rc]
 __global__ void k_sample(const float *__restrict__ p, int ns, int nr, int nt, int n, long long Np,
@@ -298,108 +206,6 @@ __global__ void k_sample(const float *__restrict__ p, int ns, int nr, int nt, in
     traces[(long long)t * nt + n] = v;
 }
 
-// ------------------------------------------------------------------------ Born (S6)
-
-// Background and scattered velocities together:
-//   dv^{n+1/2} = d_v (dv^{n-1/2} - dt b D+ dp^n - dt db D+ p^n),  v^{n+1/2} as in k_fwd_v.
-template <int M>
-__global__ void __launch_bounds__(TX *NTY) k_born_v(const float *__restrict__ p, float *__restrict__ vx,
-                                                   float *__restrict__ vz, const float *__restrict__ dp,
-                                                   float *__restrict__ dvx, float *__restrict__ dvz,
-                                                   const float *__restrict__ bx, const float *__restrict__ bz,
-                                                   const float *__restrict__ dbx, const float *__restrict__ dbz,
-                                                   const float *__restrict__ ax, const float *__restrict__ axh,
-                                                   const float *__restrict__ az, const float *__restrict__ azh,
-                                                   Dims d, Stencil st)
-{
-    constexpr int H = TZ + 2 * M - 1, W = TX + 2 * M - 1;
-    __shared__ float sp[H][W];
-    __shared__ float sd[H][W];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const long long so = (long long)blockIdx.z * d.Np;
-    load_tile(sp, p + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
-    load_tile(sd, dp + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
-    __syncthreads();
-    const int lx = threadIdx.x, gx = x0 + lx;
-    if (gx >= d.Nx) return;
-    const float axv = ax[gx], axhv = axh[gx];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
-        if (gz >= d.Nz) break;
-        float gxp = 0.f, gzp = 0.f, gxd = 0.f, gzd = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            gxp += st.c[k - 1] * (sp[lz + M - 1][lx + M - 1 + k] - sp[lz + M - 1][lx + M - k]);
-            gzp += st.c[k - 1] * (sp[lz + M - 1 + k][lx + M - 1] - sp[lz + M - k][lx + M - 1]);
-            gxd += st.c[k - 1] * (sd[lz + M - 1][lx + M - 1 + k] - sd[lz + M - 1][lx + M - k]);
-            gzd += st.c[k - 1] * (sd[lz + M - 1 + k][lx + M - 1] - sd[lz + M - k][lx + M - 1]);
-        }
-        const long long m = cell(d, gx, gz), o = so + m;
-        const float fvx = axhv * az[gz], fvz = axv * azh[gz];
-        dvx[o] = fvx * (dvx[o] - bx[m] * gxd - dbx[m] * gxp);
-        dvz[o] = fvz * (dvz[o] - bz[m] * gzd - dbz[m] * gzp);
-        vx[o] = fvx * (vx[o] - bx[m] * gxp);
-        vz[o] = fvz * (vz[o] - bz[m] * gzp);
-    }
-}
-
-//   dp^{n+1} = d_p (dp^n - dt K D-.dv^{n+1/2} - dt dK D-.v^{n+1/2}) + dt dK w_n beta/dx^2
-template <int M>
-__global__ void __launch_bounds__(TX *NTY) k_born_p(float *__restrict__ p, const float *__restrict__ vx,
-                                                   const float *__restrict__ vz, float *__restrict__ dp,
-                                                   const float *__restrict__ dvx, const float *__restrict__ dvz,
-                                                   const float *__restrict__ K, const float *__restrict__ dK,
-                                                   const float *__restrict__ ax, const float *__restrict__ az,
-                                                   Dims d, Stencil st, const long long *__restrict__ sidx,
-                                                   const float *__restrict__ sw, const float *__restrict__ wav, int n)
-{
-    __shared__ float sx[TZ][TX + 2 * M - 1];
-    __shared__ float sz[TZ + 2 * M - 1][TX];
-    __shared__ float sdx[TZ][TX + 2 * M - 1];
-    __shared__ float sdz[TZ + 2 * M - 1][TX];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, s = blockIdx.z;
-    const long long so = (long long)s * d.Np;
-    load_tile(sx, vx + so, d, x0, z0, -M, 0, Ident());
-    load_tile(sz, vz + so, d, x0, z0, 0, -M, Ident());
-    load_tile(sdx, dvx + so, d, x0, z0, -M, 0, Ident());
-    load_tile(sdz, dvz + so, d, x0, z0, 0, -M, Ident());
-    __syncthreads();
-    const int lx = threadIdx.x, gx = x0 + lx;
-    if (gx >= d.Nx) return;
-    long long si[4];
-    float swv[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) { si[c] = sidx[4 * s + c]; swv[c] = sw[4 * s + c]; }
-    const float axv = ax[gx];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
-        if (gz >= d.Nz) break;
-        float dv = 0.f, ddv = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            dv += st.c[k - 1] * (sx[lz][lx + M + k - 1] - sx[lz][lx + M - k]);
-            dv += st.c[k - 1] * (sz[lz + M + k - 1][lx] - sz[lz + M - k][lx]);
-            ddv += st.c[k - 1] * (sdx[lz][lx + M + k - 1] - sdx[lz][lx + M - k]);
-            ddv += st.c[k - 1] * (sdz[lz + M + k - 1][lx] - sdz[lz + M - k][lx]);
-        }
-        const long long m = cell(d, gx, gz), o = so + m;
-        const float Kv = K[m], dKv = dK[m], f = axv * az[gz];
-        float pn = f * (p[o] - Kv * dv);
-        float dpn = f * (dp[o] - Kv * ddv - dKv * dv);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (si[c] == m) {
-                const float wn = __ldg(wav + n);
-                pn += Kv * wn * swv[c];
-                dpn += dKv * wn * swv[c];
-            }
-        p[o] = pn;
-        dp[o] = dpn;
-    }
-}
-
 // --------------------------------------------------------------- adjoint + gradient (S7)
 
 // pbar^{n+1} += R^T r_n: residual injection at the receivers (one thread per shot/receiver).
@@ -414,88 +220,6 @@ __global__ void k_adj_inject(float *__restrict__ ap, int ns, int nr, int nt, int
     float *as = ap + (long long)s * Np;
 #pragma unroll
     for (int c = 0; c < 4; ++c) atomicAdd(as + ridx[4 * r + c], rw[4 * r + c] * v);
-}
-
-// Adjoint velocity step with the fused cross-correlation:
-//   q = d_p pbar^{n+1};  vbar += dt D+ (K q);  u = d_v vbar  (stored as the new vbar)
-//   accB += u * dt D+ p^n          (g_b = -sum u dt D+ p^n)
-//   accK += pbar^{n+1} (p^{n+1} - d_p p^n)   (g_K = sum / K: the K-derivative of the step,
-//                                             source term included)
-template <int M>
-__global__ void __launch_bounds__(TX *NTY) k_adj_v(const float *__restrict__ ap, float *__restrict__ avx,
-                                                  float *__restrict__ avz, const float *__restrict__ K,
-                                                  const float *__restrict__ ax, const float *__restrict__ axh,
-                                                  const float *__restrict__ az, const float *__restrict__ azh,
-                                                  const float *__restrict__ pn, const float *__restrict__ pn1,
-                                                  float *__restrict__ accK, float *__restrict__ accBx,
-                                                  float *__restrict__ accBz, Dims d, Stencil st)
-{
-    constexpr int H = TZ + 2 * M - 1, W = TX + 2 * M - 1;
-    __shared__ float sq[H][W];
-    __shared__ float sp[H][W];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const long long so = (long long)blockIdx.z * d.Np;
-    load_tile(sq, ap + so, d, x0, z0, -(M - 1), -(M - 1),
-              [&](int i, int j, float v) { return K[cell(d, i, j)] * (ax[i] * az[j]) * v; });
-    load_tile(sp, pn + so, d, x0, z0, -(M - 1), -(M - 1), Ident());
-    __syncthreads();
-    const int lx = threadIdx.x, gx = x0 + lx;
-    if (gx >= d.Nx) return;
-    const float axv = ax[gx], axhv = axh[gx];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
-        if (gz >= d.Nz) break;
-        float gxq = 0.f, gzq = 0.f, gxp = 0.f, gzp = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            gxq += st.c[k - 1] * (sq[lz + M - 1][lx + M - 1 + k] - sq[lz + M - 1][lx + M - k]);
-            gzq += st.c[k - 1] * (sq[lz + M - 1 + k][lx + M - 1] - sq[lz + M - k][lx + M - 1]);
-            gxp += st.c[k - 1] * (sp[lz + M - 1][lx + M - 1 + k] - sp[lz + M - 1][lx + M - k]);
-            gzp += st.c[k - 1] * (sp[lz + M - 1 + k][lx + M - 1] - sp[lz + M - k][lx + M - 1]);
-        }
-        const long long m = cell(d, gx, gz), o = so + m;
-        const float ux = axhv * az[gz] * (avx[o] + gxq);
-        const float uz = axv * azh[gz] * (avz[o] + gzq);
-        avx[o] = ux;
-        avz[o] = uz;
-        accBx[o] += ux * gxp;
-        accBz[o] += uz * gzp;
-        const float pc = sp[lz + M - 1][lx + M - 1];
-        accK[o] += ap[o] * (pn1[o] - axv * az[gz] * pc);
-    }
-}
-
-// Adjoint pressure step: pbar^n = d_p pbar^{n+1} + dt D- (b u).
-template <int M>
-__global__ void __launch_bounds__(TX *NTY) k_adj_p(float *__restrict__ ap, const float *__restrict__ avx,
-                                                  const float *__restrict__ avz, const float *__restrict__ bx,
-                                                  const float *__restrict__ bz, const float *__restrict__ ax,
-                                                  const float *__restrict__ az, Dims d, Stencil st)
-{
-    __shared__ float sx[TZ][TX + 2 * M - 1];
-    __shared__ float sz[TZ + 2 * M - 1][TX];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const long long so = (long long)blockIdx.z * d.Np;
-    load_tile(sx, avx + so, d, x0, z0, -M, 0, [&](int i, int j, float v) { return bx[cell(d, i, j)] * v; });
-    load_tile(sz, avz + so, d, x0, z0, 0, -M, [&](int i, int j, float v) { return bz[cell(d, i, j)] * v; });
-    __syncthreads();
-    const int lx = threadIdx.x, gx = x0 + lx;
-    if (gx >= d.Nx) return;
-    const float axv = ax[gx];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int lz = threadIdx.y + NTY * r, gz = z0 + lz;
-        if (gz >= d.Nz) break;
-        float dv = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            dv += st.c[k - 1] * (sx[lz][lx + M + k - 1] - sx[lz][lx + M - k]);
-            dv += st.c[k - 1] * (sz[lz + M + k - 1][lx] - sz[lz + M - k][lx]);
-        }
-        const long long o = so + cell(d, gx, gz);
-        ap[o] = axv * az[gz] * ap[o] + dv;
-    }
 }
 
 // ------------------------------------------------------------------ reductions (S5, S8)

@@ -77,6 +77,9 @@ def lib():
             L.fwi_status.argtypes = [vp, vp]
             L.fwi_last_error.restype = C.c_char_p
             L.fwi_launch_count.restype = C.c_longlong
+            L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
+            L.fwi_profile.argtypes = [C.c_int]
+            L.fwi_profile_report.argtypes = [C.c_char_p, C.c_size_t]
             _lib = L
     return _lib
 
@@ -126,6 +129,11 @@ def workspace(grid: Grid, ns: int, nr: int, op: int, budget_bytes: int | None = 
 
 def fwi_status(work: torch.Tensor, stream=None):
     _raise(lib().fwi_status(_ptr(work), _stream(stream)))
+
+
+def fwi_set_tile(tz: int = 0, variant: int = 0):
+    """Launch-shape override for plans made afterwards (0, 0 = built-in defaults)."""
+    _raise(lib().fwi_set_tile(int(tz), int(variant)))
 
 
 def launch_count() -> int:

@@ -134,26 +134,37 @@ def test_model_shot_groups_bitwise(F):
 # -------------------------------------------------------------------- full-size workloads
 
 def test_config_point_full(F):
-    """201 x 201 + 40-cell sponge, 4th order, 800 steps, 8 sources / 64 receivers: traces and
-    K-rho gradient (the record at 800 steps ends before the scattered arrivals; the gradient
-    is also checked at 1400 steps, where they are inside the record)."""
+    """201 x 201 + 40-cell sponge, 4th order, 800 steps, 8 sources / 64 receivers: traces, and
+    the gradient at 1400 steps (at 800 the record ends before the scattered arrivals).
+
+    The point scatterer's residual is ~3e-4 of the traces, so the FP32 trace error (~5e-7)
+    becomes a ~2e-3 error of the residual itself: the gradient tolerance is checked on the
+    adjoint given the oracle's residual, and fwi_gradient is checked against fwi_adjoint fed
+    with the residual of its own forward traces."""
     for nt in (800, 1400):
         w = I.config_point(nt)
         og = oracle_grid(w)
         tr = run_model(F, w)
         ref = oracle.model(og, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
         assert rel_l2(tr, ref) <= TRACE_TOL
-        if nt == 800:   # residual would be FP32 noise only: nothing scattered has arrived
+        if nt == 800:
             continue
         a0, b0 = w.background()
         data = ref.astype(np.float32)
-        J_ref, G_ref = oracle.gradient(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
-        J, G = F.fwi_gradient(gpu_grid(w), w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
-        assert abs(J.item() - J_ref) <= 1e-3 * J_ref
-        G = G.cpu().numpy()
+        bg_ref = oracle.model(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy)
+        res_ref = (bg_ref - data).astype(np.float32)
+        g = gpu_grid(w)
+        G = F.fwi_adjoint(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, res_ref).cpu().numpy()
+        G_ref = oracle.adjoint(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, res_ref)
         for pz in range(5):
             for k in range(2):
-                assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL, (nt, pz, k)
+                assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL, (pz, k)
+        J, Gg = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
+        J_ref = 0.5 * float(np.sum(res_ref.astype(np.float64) ** 2))
+        assert abs(J.item() - J_ref) <= 1e-2 * J_ref
+        bg = run_model(F, w, a0, b0)
+        Gs = F.fwi_adjoint(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, bg - data).cpu().numpy()
+        assert rel_l2(Gg.cpu().numpy(), Gs) <= 1e-6
 
 
 def test_config_gaussian_full_traces_sampled(F):
@@ -225,3 +236,30 @@ def test_errors_reported(F):
     assert e.value.code == -3
     # the context is still usable
     run_model(F, w)
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_poisoned_workspace_gives_identical_results(F, order):
+    """A workspace full of NaN bytes before every call gives bit-identical traces, Born traces
+    and gradients: no kernel reads memory that the operation has not written."""
+    w = I.small_case(seed=60 + order, nx=37, nz=29, nt=90, order=order, sponge=5, ns=3, nr=4)
+    g = gpu_grid(w)
+    da, db = I.random_like(w.xi_a.shape, 1, 0.05), I.random_like(w.xi_a.shape, 2, 0.05)
+    data = run_model(F, w, w.xi_a * 1.2, w.xi_b * 0.9)
+    out = []
+    for poison in (False, True):
+        ws = {op: F.workspace(g, w.ns, w.nr, op, 1 << 34) for op in (F.OP_MODEL, F.OP_BORN, F.OP_GRADIENT)}
+        if poison:
+            for t in ws.values():
+                t.fill_(0xFF)       # every float32 becomes NaN
+        tr = run_model(F, w, work=ws[F.OP_MODEL])
+        bo = F.fwi_born(g, w.pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy,
+                        work=ws[F.OP_BORN]).cpu().numpy()
+        J, G = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, data, work=ws[F.OP_GRADIENT])
+        out.append((tr, bo, J.item(), G.cpu().numpy()))
+    (t0, b0, J0, G0), (t1, b1, J1, G1) = out
+    assert np.all(np.isfinite(t1)) and np.all(np.isfinite(b1)) and np.all(np.isfinite(G1))
+    np.testing.assert_array_equal(t0, t1)
+    np.testing.assert_array_equal(b0, b1)
+    assert J0 == J1
+    np.testing.assert_array_equal(G0, G1)
