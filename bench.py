@@ -36,15 +36,15 @@ sys.path.insert(0, ROOT)
 METRIC = "Gcell-updates/s & FWI gradients/s vs plain per-shot GPU; p50/p99 solve latency"
 UNIT = "Gcell-updates/s"
 
-# Algorithmic HBM bytes per computational cell and shot for one launch of each stencil kernel
-# (FP32 fields: reads + writes each field once); model arrays shared by the shots of a
-# launch are counted once per launch (MODEL_BYTES per cell).
+# Algorithmic HBM bytes per computational cell and shot for one launch of each time-step kernel
+# (FP32 fields, each read or written once), and model bytes per cell counted once per launch
+# (the model arrays are shared by every shot of the launch).
 KERNEL_BYTES = {
-    "k_fwd_v": 20, "k_fwd_p<false>": 16, "k_fwd_p<true>": 20,
-    "k_adj_v": 52, "k_adj_p": 16,
-    "k_born_v": 40, "k_born_p": 32,
+    "k_fwd_warp": 24,    # p^n, vx, vz read; p^{n+1}, vx, vz written
+    "k_adj_warp": 52,    # pbar, vbar read+written (24), p^n snapshot (4), g_K, g_bx, g_bz accumulated (24)
+    "k_born_warp": 48,   # background and scattered p, vx, vz read and written
 }
-MODEL_BYTES = {"k_fwd_v": 8, "k_fwd_p": 4, "k_adj_v": 4, "k_adj_p": 8, "k_born_v": 16, "k_born_p": 8}
+MODEL_BYTES = {"k_fwd_warp": 12, "k_adj_warp": 12, "k_born_warp": 24}
 
 
 def parse():
@@ -281,13 +281,12 @@ def main():
     total_dev = sum(v[1] for v in prof.values()) or 1.0
     for name, (cnt, tot) in prof.items():
         short = name.split("::")[-1].split("<")[0]
-        kernels[name.replace("fwi::", "").replace("(", "").replace(")", "")] = {
+        kernels[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = {
             "launches": cnt, "ms": round(tot, 3), "share": round(tot / total_dev, 4)}
     if dom:
         name, (cnt, tot) = dom
-        short = name.split("::")[-1].split("<")[0]
-        key = short + ("<true>" if "true" in name else "<false>" if "false" in name else "")
-        per_cell = KERNEL_BYTES.get(key, KERNEL_BYTES.get(short))
+        short = name.split("::")[-1].split("<")[0].strip("(")
+        per_cell = KERNEL_BYTES.get(short)
         if per_cell:
             # shots per launch: every launch of the timed region covers the whole group
             B = ns

@@ -139,8 +139,8 @@ long long fwi_launch_count(void);
 
 /* Launch-shape tuning (no counterpart in the paper: the autotuner's hook).  Sets, for plans
  * made afterwards by any thread, the strip height of the streaming kernels (multiple of 8;
- * 0 = built-in default) and the kernel variant (0 = full register budget, 1 = at most 128
- * registers per thread).  Results are identical for every setting; only speed changes. */
+ * 0 = built-in default) and the kernel variant (register budget per thread: 0 = unbounded,
+ * 1 = 128, 2 = 170).  Results are identical for every setting; only speed changes. */
 int fwi_set_tile(int tz, int variant);
 
 /* Per-launch timing (no counterpart in the paper: measurement support).  While enabled,

@@ -93,8 +93,7 @@ struct Plan {
     int C = 0;        // steps per snapshot segment (== nt: whole history kept)
     int nseg = 1;     // segments
     int ngroups = 0;
-    int NT = 0;       // threads of a row-streaming CTA (4 columns each)
-    int tz = 0;       // rows per row-streaming CTA / warp strip
+    int tz = 0;       // rows per warp strip
     int variant = 0;  // kernel variant (register budget) chosen by the tuner
     // byte offsets into the workspace
     size_t status = 0, K = 0, bx = 0, bz = 0, ax = 0, axh = 0, az = 0, azh = 0;
@@ -133,7 +132,6 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
         P.st.c[k] = (float)(c * g->dt / g->dx);
     }
     P.ns = ns; P.nr = nr; P.nt = g->nt;
-    P.NT = (int)up((size_t)(d.Nx + 3) / 4, 32);
     P.tz = g_tile_tz > 0 ? g_tile_tz : 64;
     P.variant = g_tile_variant;
     P.B = std::max(1, std::min(B, std::max(ns, 1)));
@@ -280,22 +278,11 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
     return FWI_OK;
 }
 
-// Row-streaming launch shape: grid (strips, shots), block NT, dynamic shared memory for
-// (rings + 2) shared rows.
-dim3 strips(const Plan &P, int shots) { return dim3((P.d.Nz + P.tz - 1) / P.tz, shots); }
-size_t stream_smem(const Plan &P, int rows) { return (size_t)rows * (4 * P.NT + 2 * fwi::SHALO) * sizeof(float); }
-
-template <typename K>
-void allow_smem(K kernel, size_t bytes)
-{
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// Warp-strip launch shape: one warp per (128-column strip, tz-row strip, shot), 2 warps a block.
-dim3 warp_grid(const Plan &P, int shots)
+// Warp-strip launch shape: one warp per (128-column strip, tz-row strip, shot), wpb warps a block.
+dim3 warp_grid(const Plan &P, int shots, int wpb = 2)
 {
     const long long warps = (long long)((P.d.Nx + fwi::WS - 1) / fwi::WS) * ((P.d.Nz + P.tz - 1) / P.tz) * shots;
-    return dim3((unsigned)((warps + 1) / 2));
+    return dim3((unsigned)((warps + wpb - 1) / wpb));
 }
 
 fwi::Model model_of(const Plan &P, void *work)
@@ -321,17 +308,20 @@ struct Fwd {
         const dim3 grid = warp_grid(P, bg);
         const fwi::Model mo = model_of(P, work);
         if (P.M == 2) {
-            if (P.variant == 1)
-                LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
-            else
-                LAUNCH((fwi::k_fwd_warp<2, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
+            switch (P.variant) {
+            case 1: LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
+            case 2: LAUNCH((fwi::k_fwd_warp<2, 6>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
+            default: LAUNCH((fwi::k_fwd_warp<2, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
+            }
         } else {
-            if (P.variant == 1)
-                LAUNCH((fwi::k_fwd_warp<4, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
-            else
-                LAUNCH((fwi::k_fwd_warp<4, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
+            switch (P.variant) {
+            case 1: LAUNCH((fwi::k_fwd_warp<4, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
+            case 2: LAUNCH((fwi::k_fwd_warp<4, 6>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
+            default: LAUNCH((fwi::k_fwd_warp<4, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
+            }
         }
     }
+
     void sample(int n, int bg, int nr, const float *p, float *traces) const
     {
         if (nr == 0) return;
@@ -417,23 +407,28 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
         for (int n = n1 - 1; n >= n0; --n) {
             const int i = (n + 1) & 1, o = n & 1;
             float *ap0 = at<float>(work, P.ap[i]);
-            if (P.nr > 0)
-                LAUNCH(fwi::k_adj_inject, (bg * P.nr + 127) / 128, 128, 0, st, ap0, bg, P.nr, P.nt, n, d.Np,
-                       at<long long>(work, P.ridx), at<float>(work, P.rw), res);
             const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
+            if (P.nr > 0)
+                LAUNCH(fwi::k_adj_inject_k, (bg * P.nr + 127) / 128, 128, 0, st, ap0, aK, pn1, bg, P.nr, P.nt, n, d.Np,
+                       at<long long>(work, P.ridx), at<float>(work, P.rw), res);
             const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
             float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
+            const dim3 grid = warp_grid(P, bg, 1);
+#define ADJ_ARGS ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, P.tz, bg
             if (P.M == 2) {
-                const size_t sm = stream_smem(P, 4 * 2 + 2);
-                allow_smem(fwi::k_adj_stream<2>, sm);
-                LAUNCH(fwi::k_adj_stream<2>, strips(P, bg), P.NT, sm, st, ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, pn1,
-                       aK, aBx, aBz, d, P.st, P.tz);
+                switch (P.variant) {
+                case 1: LAUNCH((fwi::k_adj_warp<2, 8>), grid, 32, 0, st, ADJ_ARGS); break;
+                case 2: LAUNCH((fwi::k_adj_warp<2, 6>), grid, 32, 0, st, ADJ_ARGS); break;
+                default: LAUNCH((fwi::k_adj_warp<2, 1>), grid, 32, 0, st, ADJ_ARGS);
+                }
             } else {
-                const size_t sm = stream_smem(P, 4 * 4 + 2);
-                allow_smem(fwi::k_adj_stream<4>, sm);
-                LAUNCH(fwi::k_adj_stream<4>, strips(P, bg), P.NT, sm, st, ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, pn1,
-                       aK, aBx, aBz, d, P.st, P.tz);
+                switch (P.variant) {
+                case 1: LAUNCH((fwi::k_adj_warp<4, 8>), grid, 32, 0, st, ADJ_ARGS); break;
+                case 2: LAUNCH((fwi::k_adj_warp<4, 6>), grid, 32, 0, st, ADJ_ARGS); break;
+                default: LAUNCH((fwi::k_adj_warp<4, 1>), grid, 32, 0, st, ADJ_ARGS);
+                }
             }
+#undef ADJ_ARGS
         }
     }
     return FWI_OK;
@@ -563,17 +558,17 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
             const int i = n & 1, o = (n + 1) & 1;
             auto F = [&](const size_t *a) { return at<float>(work, a[i]); };
             auto G = [&](const size_t *a) { return at<float>(work, a[o]); };
+            const dim3 grid = warp_grid(P, bg, 1);
+#define BORN_ARGS F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), G(P.vz), G(P.dp), \
+                  G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz, bg
             if (P.M == 2) {
-                const size_t sm = stream_smem(P, 4 * 2 + 4);
-                allow_smem(fwi::k_born_stream<2>, sm);
-                LAUNCH(fwi::k_born_stream<2>, strips(P, bg), P.NT, sm, st, F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx),
-                       F(P.dvz), G(P.p), G(P.vx), G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz);
+                if (P.variant == 2) LAUNCH((fwi::k_born_warp<2, 12>), grid, 32, 0, st, BORN_ARGS);
+                else LAUNCH((fwi::k_born_warp<2, 1>), grid, 32, 0, st, BORN_ARGS);
             } else {
-                const size_t sm = stream_smem(P, 4 * 4 + 4);
-                allow_smem(fwi::k_born_stream<4>, sm);
-                LAUNCH(fwi::k_born_stream<4>, strips(P, bg), P.NT, sm, st, F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx),
-                       F(P.dvz), G(P.p), G(P.vx), G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz);
+                if (P.variant == 2) LAUNCH((fwi::k_born_warp<4, 12>), grid, 32, 0, st, BORN_ARGS);
+                else LAUNCH((fwi::k_born_warp<4, 1>), grid, 32, 0, st, BORN_ARGS);
             }
+#undef BORN_ARGS
             if (P.nr > 0)
                 LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, G(P.dp), bg, P.nr, P.nt, n, d.Np,
                        at<long long>(work, P.ridx), at<float>(work, P.rw), out);
@@ -632,7 +627,8 @@ const char *fwi_last_error(void) { return g_err.c_str(); }
 
 int fwi_set_tile(int tz, int variant)
 {
-    if (tz < 0 || tz % 8 || variant < 0 || variant > 1) return fail(FWI_EINVAL, "tile height must be a multiple of 8, variant 0 or 1");
+    if (tz < 0 || tz % 8 || variant < 0 || variant > 2)
+        return fail(FWI_EINVAL, "tile height must be a multiple of 8, variant 0, 1 or 2");
     g_tile_tz = tz;
     g_tile_variant = variant;
     return FWI_OK;

@@ -208,20 +208,6 @@ __global__ void k_sample(const float *__restrict__ p, int ns, int nr, int nt, in
 
 // --------------------------------------------------------------- adjoint + gradient (S7)
 
-// pbar^{n+1} += R^T r_n: residual injection at the receivers (one thread per shot/receiver).
-__global__ void k_adj_inject(float *__restrict__ ap, int ns, int nr, int nt, int n, long long Np,
-                             const long long *__restrict__ ridx, const float *__restrict__ rw,
-                             const float *__restrict__ res)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ns * nr) return;
-    const int s = t / nr, r = t - s * nr;
-    const float v = res[(long long)t * nt + n];
-    float *as = ap + (long long)s * Np;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) atomicAdd(as + ridx[4 * r + c], rw[4 * r + c] * v);
-}
-
 // ------------------------------------------------------------------ reductions (S5, S8)
 
 constexpr int RED_THREADS = 256;
