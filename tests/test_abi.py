@@ -50,9 +50,9 @@ def test_workspace_planning(L):
     assert big >= 3001 * 64 * Np
     mid = fwi.fwi_workspace_bytes(g, 64, 256, fwi.OP_GRADIENT, 150 << 30)
     assert mn <= mid <= 150 << 30
-    # forward only needs the model and three state fields per shot
+    # forward only needs the model and the ping-ponged state (2 x p, vx, vz) of every shot
     m = fwi.fwi_workspace_bytes(g, 64, 256, fwi.OP_MODEL, 1 << 50)
-    assert 3 * 64 * Np <= m <= 4 * 64 * Np + (64 << 20)
+    assert 6 * 64 * Np <= m <= 7 * 64 * Np + (64 << 20)
     # invalid arguments -> 0 -> error
     bad = fwi.make_grid(601, 601, 5.0, 5e-4, 3000, order=6)
     with pytest.raises(fwi.FwiError):
