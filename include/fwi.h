@@ -137,6 +137,31 @@ const char *fwi_last_error(void);
 /* Kernels launched by the last operation on this thread (for launch accounting). */
 long long fwi_launch_count(void);
 
+/* Forward modelling without any device allocation (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc or any allocating routine where they need a
+ * forward model: a service whose device memory is fixed at start-up, a plugin inside a
+ * framework that owns all device memory, code where an allocation may block on other work.
+ * Same arguments and results as fwi_model, without work/work_bytes: the scratch is a
+ * file-scope __device__ array of FWI_NOALLOC_SCRATCH_BYTES (64 MiB) in the library image,
+ * which every GPU that loads the library holds until the process exits.
+ *  - Limit: the grid, shot and receiver counts must fit that scratch with one shot at a
+ *    time (fwi_workspace_bytes(g, ns, nr, FWI_OP_MODEL, 0) <= FWI_NOALLOC_SCRATCH_BYTES,
+ *    e.g. 201 x 201 + 40-cell sponge with 64 shots); larger problems return FWI_ENOMEM
+ *    with a message in fwi_last_error().
+ *  - The first call on a device resolves the scratch address on that device (the device
+ *    must be current); make that first call before any stream capture.
+ *  - All calls share the one scratch array per device and it keeps the last call's
+ *    contents; the call clears what must start at zero.  Calls whose work overlaps on the
+ *    GPU (different streams, or different host threads) race on the scratch: serialise them.
+ *  - The data-dependent checks fwi_model records in its workspace (1 + xi <= 0, CFL, points
+ *    off the grid) land in the scratch, which fwi_status() cannot reach: validate those
+ *    inputs beforehand.  Host-visible argument errors are returned as usual.
+ */
+#define FWI_NOALLOC_SCRATCH_BYTES (64u << 20)
+int fwi_model_noalloc(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+                      const fwi_sources *src, const fwi_receivers *rec, float *traces, void *stream);
+
 /* Launch-shape tuning (no counterpart in the paper: the autotuner's hook).  Sets, for plans
  * made afterwards by any thread, the strip height of the streaming kernels (multiple of 8;
  * 0 = built-in default) and the kernel variant (register budget per thread: 0 = unbounded,

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfwi.so")
-SOURCES = [os.path.join(CSRC, "fwi_api.cu")]
+SOURCES = [os.path.join(CSRC, "fwi_api.cu"), os.path.join(CSRC, "fwi_noalloc.cu")]
 DEPS = SOURCES + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".cu", ".h"))) + \
     [os.path.join(ROOT, "include", "fwi.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

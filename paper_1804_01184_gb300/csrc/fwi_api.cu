@@ -494,6 +494,10 @@ int adjoint_impl(const fwi_grid *g, int pz, const float *xa, const float *xb, co
 
 }  // namespace
 
+namespace fwi_internal {
+void set_error(const char *msg) { g_err = msg ? msg : ""; }
+}
+
 extern "C" {
 
 size_t fwi_workspace_bytes(const fwi_grid *g, int ns, int nr, fwi_op op, size_t budget_bytes)

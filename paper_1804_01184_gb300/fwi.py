@@ -78,6 +78,7 @@ def lib():
             L.fwi_last_error.restype = C.c_char_p
             L.fwi_launch_count.restype = C.c_longlong
             L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
+            L.fwi_model_noalloc.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp]
             L.fwi_profile.argtypes = [C.c_int]
             L.fwi_profile_report.argtypes = [C.c_char_p, C.c_size_t]
             _lib = L
@@ -158,6 +159,19 @@ def fwi_model(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, traces=N
                            _ptr(work), work.numel(), _stream(stream)))
     if check:
         fwi_status(work, stream)
+    return traces
+
+
+def fwi_model_noalloc(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, traces=None,
+                      stream=None) -> torch.Tensor:
+    """fwi_model on the library's built-in scratch, for callers that cannot allocate device
+    memory (see fwi_model_noalloc in include/fwi.h: size limit, first-call set-up, sharing)."""
+    a, b = _dev(xi_a), _dev(xi_b)
+    keep, S, R = _acq(src_xy, wavelet, rec_xy)
+    if traces is None:
+        traces = torch.empty((S.ns, R.nr, grid.nt), dtype=torch.float32, device="cuda")
+    _raise(lib().fwi_model_noalloc(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R),
+                                   _ptr(traces), _stream(stream)))
     return traces
 
 
