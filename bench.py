@@ -47,6 +47,32 @@ KERNEL_BYTES = {
 MODEL_BYTES = {"k_fwd_warp": 12, "k_adj_warp": 12, "k_born_warp": 24}
 
 
+def short_name(launch_name):
+    """'(fwi::k_fwd_warp<4, 1>)' -> 'k_fwd_warp'"""
+    return launch_name.split("::")[-1].split("<")[0].strip("()")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fwi_warp.cuh", "fwi_stream.cuh", "fwi_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1804_01184_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, shots):
+    """DRAM bytes (read + write) per launch from the committed ncu capture, scaled to `shots`
+    shots per launch; None when the kernels changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    t = json.load(open(path))
+    if t.get("kernel_source_sha256") != kernel_source_hash() or kernel not in t.get("kernels", {}):
+        return None
+    k = t["kernels"][kernel]
+    return int(k["dram_bytes_per_launch"] * shots / k["shots_per_launch"])
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,34 +295,34 @@ def main():
     grads_per_s = args.steps * world / (ms / 1e3)
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
-    import json as _j
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
-        peaks = _j.load(open(pk_path))
+        peaks = json.load(open(pk_path))
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
-    roof = None
-    kernels = {}
     total_dev = sum(v[1] for v in prof.values()) or 1.0
+    kernels = {}
     for name, (cnt, tot) in prof.items():
-        short = name.split("::")[-1].split("<")[0]
         kernels[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = {
             "launches": cnt, "ms": round(tot, 3), "share": round(tot / total_dev, 4)}
+    # shot-steps each time-step kernel performs per bench step: the forward runs in fwi_model
+    # and in fwi_gradient, the adjoint in fwi_gradient, Born in fwi_born
+    shot_steps = {"k_fwd_warp": 2 * ns * nt, "k_adj_warp": ns * nt, "k_born_warp": ns * nt}
+    roof = None
+    dom = max(((n, v) for n, v in prof.items() if short_name(n) in KERNEL_BYTES), key=lambda kv: kv[1][1],
+              default=None)
     if dom:
         name, (cnt, tot) = dom
-        short = name.split("::")[-1].split("<")[0].strip("(")
-        per_cell = KERNEL_BYTES.get(short)
-        if per_cell:
-            # shots per launch: every launch of the timed region covers the whole group
-            B = ns
-            bytes_per_launch = cells * (per_cell * B + MODEL_BYTES.get(short, 0))
-            avg_s = tot / cnt / 1e3
-            achieved = bytes_per_launch / avg_s / 1e9
-            roof = {"kernel": short, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
-                    "bytes_per_launch": bytes_per_launch, "avg_launch_us": round(avg_s * 1e6, 2),
-                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        short = short_name(name)
+        shots = shot_steps[short] * args.steps / cnt          # average shots per launch
+        bytes_per_launch = cells * (KERNEL_BYTES[short] * shots + MODEL_BYTES[short])
+        avg_s = tot / cnt / 1e3
+        achieved = bytes_per_launch / avg_s / 1e9
+        roof = {"kernel": short, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": measured_traffic(short, shots),
+                "bytes_per_launch": int(bytes_per_launch), "shots_per_launch": round(shots, 2),
+                "avg_launch_us": round(avg_s * 1e6, 2),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
