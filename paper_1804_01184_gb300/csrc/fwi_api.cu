@@ -130,6 +130,7 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
     for (int k = 0; k < 4; ++k) {
         double c = k < P.M ? (P.M == 2 ? c4[k] : c8[k]) : 0.0;
         P.st.c[k] = (float)(c * g->dt / g->dx);
+        P.st.nc[k] = -P.st.c[k];
     }
     P.ns = ns; P.nr = nr; P.nt = g->nt;
     P.tz = g_tile_tz > 0 ? g_tile_tz : 64;

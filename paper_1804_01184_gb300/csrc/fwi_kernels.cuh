@@ -25,9 +25,11 @@ struct Dims {
     long long Np;         // Px * Nz: floats per field per shot
 };
 
-// c_k * dt / dx: the stencil weights with the time step and spacing folded in
+// c_k * dt / dx: the stencil weights with the time step and spacing folded in, and their
+// negatives (a subtracted stencil term becomes one fused multiply-add)
 struct Stencil {
     float c[4];
+    float nc[4];
 };
 
 // status bits recorded by the kernels

@@ -12,6 +12,47 @@ namespace fwi {
 constexpr int SHALO = 4;   // zero columns on each side of a shared row (one float4)
 
 __device__ __forceinline__ float4 f4(float v) { return make_float4(v, v, v, v); }
+
+// Packed FP32x2 arithmetic (sm_100+): two lanes of a float4 per instruction, each component
+// rounded exactly as the scalar operation.
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// a * b + c
+__device__ __forceinline__ float4 pfma(const float4 &a, const float4 &b, const float4 &c)
+{
+    return cat4(__ffma2_rn(lo2(a), lo2(b), lo2(c)), __ffma2_rn(hi2(a), hi2(b), hi2(c)));
+}
+// s * b + c
+__device__ __forceinline__ float4 pfma(float s, const float4 &b, const float4 &c)
+{
+    const float2 s2 = make_float2(s, s);
+    return cat4(__ffma2_rn(s2, lo2(b), lo2(c)), __ffma2_rn(s2, hi2(b), hi2(c)));
+}
+__device__ __forceinline__ float4 pmul(const float4 &a, const float4 &b)
+{
+    return cat4(__fmul2_rn(lo2(a), lo2(b)), __fmul2_rn(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 pmul(float s, const float4 &b)
+{
+    const float2 s2 = make_float2(s, s);
+    return cat4(__fmul2_rn(s2, lo2(b)), __fmul2_rn(s2, hi2(b)));
+}
+__device__ __forceinline__ float4 padd(const float4 &a, const float4 &b)
+{
+    return cat4(__fadd2_rn(lo2(a), lo2(b)), __fadd2_rn(hi2(a), hi2(b)));
+}
+// a - b (b * -1 + a: exact product, one rounding)
+__device__ __forceinline__ float4 psub(const float4 &a, const float4 &b)
+{
+    const float2 m = make_float2(-1.f, -1.f);
+    return cat4(__ffma2_rn(lo2(b), m, lo2(a)), __ffma2_rn(hi2(b), m, hi2(a)));
+}
+// c + s * (a - b): one stencil tap on a float4
+__device__ __forceinline__ float4 ptap(float s, const float4 &a, const float4 &b, const float4 &c)
+{
+    return pfma(s, psub(a, b), c);
+}
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
@@ -40,7 +81,7 @@ __device__ __forceinline__ float4 mask4(float4 v, int c0, int Nx)
 // D+ along x of a shared row at the four half nodes c0+1/2 .. c0+3+1/2 (c0 = 4*tid):
 // sum_k c_k (f[i+k] - f[i-k+1]) needs columns c0-3 .. c0+7 = three aligned float4.
 template <int M>
-__device__ __forceinline__ float4 row_dplus(const float *row, int c0, const Stencil &st)
+__device__ __forceinline__ float4 row_dplus(const float *row, int c0, const float *cf)
 {
     float w[12];
     const float4 a = ld4(row + c0 - 4), b = ld4(row + c0), c = ld4(row + c0 + 4);
@@ -51,7 +92,7 @@ __device__ __forceinline__ float4 row_dplus(const float *row, int c0, const Sten
     for (int q = 0; q < 4; ++q) {
         float g = 0.f;
 #pragma unroll
-        for (int k = 1; k <= M; ++k) g = fmaf(st.c[k - 1], w[4 + q + k] - w[4 + q - k + 1], g);
+        for (int k = 1; k <= M; ++k) g = fmaf(cf[k - 1], w[4 + q + k] - w[4 + q - k + 1], g);
         o[q] = g;
     }
     return make_float4(o[0], o[1], o[2], o[3]);
@@ -60,7 +101,7 @@ __device__ __forceinline__ float4 row_dplus(const float *row, int c0, const Sten
 // D- along x of a shared half-node row at the four nodes c0 .. c0+3:
 // sum_k c_k (g[i+k-1] - g[i-k]) needs columns c0-4 .. c0+6.
 template <int M>
-__device__ __forceinline__ float4 row_dminus(const float *row, int c0, const Stencil &st)
+__device__ __forceinline__ float4 row_dminus(const float *row, int c0, const float *cf)
 {
     float w[12];
     const float4 a = ld4(row + c0 - 4), b = ld4(row + c0), c = ld4(row + c0 + 4);
@@ -71,7 +112,7 @@ __device__ __forceinline__ float4 row_dminus(const float *row, int c0, const Ste
     for (int q = 0; q < 4; ++q) {
         float g = 0.f;
 #pragma unroll
-        for (int k = 1; k <= M; ++k) g = fmaf(st.c[k - 1], w[4 + q + k - 1] - w[4 + q - k], g);
+        for (int k = 1; k <= M; ++k) g = fmaf(cf[k - 1], w[4 + q + k - 1] - w[4 + q - k], g);
         o[q] = g;
     }
     return make_float4(o[0], o[1], o[2], o[3]);
