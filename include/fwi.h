@@ -162,11 +162,82 @@ long long fwi_launch_count(void);
 int fwi_model_noalloc(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
                       const fwi_sources *src, const fwi_receivers *rec, float *traces, void *stream);
 
+/* Wavefield checkpointing (no counterpart in the paper: the adjoint needs the forward
+ * wavefield, Sec. "Scheme III").  every > 0: plans made afterwards for fwi_adjoint and
+ * fwi_gradient keep (p, vx, vz) checkpoints every `every` steps and recompute each segment's
+ * pressure history before its adjoint, whatever the budget allows; 0 (default): the planner
+ * keeps the whole history when it fits and otherwise checkpoints every ~sqrt(3 nt) steps.
+ * Gradients are identical either way. */
+int fwi_set_checkpoint(int every);
+
 /* Launch-shape tuning (no counterpart in the paper: the autotuner's hook).  Sets, for plans
  * made afterwards by any thread, the strip height of the streaming kernels (multiple of 8;
  * 0 = built-in default) and the kernel variant (register budget per thread: 0 = unbounded,
  * 1 = 128, 2 = 170).  Results are identical for every setting; only speed changes. */
 int fwi_set_tile(int tz, int variant);
+
+/* ---------------------------------------------------------------------------------------
+ * Batching engine (no counterpart in the paper: the throughput layer for many independent
+ * problems -- shots of different surveys, line searches, sweeps over models).
+ *
+ * An engine owns a caller-allocated device arena (256-byte aligned; the engine never
+ * allocates device memory) and one stream.  fwi_engine_submit() queues a job; jobs are
+ * admitted first-in first-out whenever their workspace (the plan the job's work_budget
+ * gives) fits into the free part of the arena (first-fit), and it returns to the arena
+ * when they finish, so new jobs join while earlier ones still run.
+ * fwi_engine_run() advances every admitted job by one time step per iteration; the steps of
+ * all running jobs of one kind go out as one batched kernel launch (up to 96 jobs per
+ * launch, larger batches split).  Each job computes exactly what the matching single-job
+ * call (fwi_model, fwi_born, fwi_gradient) computes with a workspace of
+ * fwi_workspace_bytes(grid, ns, nr, op, work_budget) bytes: its results are bitwise
+ * independent of the other jobs it runs beside.
+ *
+ * A job's input arrays (contrasts, geometry, wavelet, data) and outputs stay owned by the
+ * caller and must stay valid until the job's ticket comes back as done.  Data-dependent
+ * errors (CFL, points off the grid) are recorded in the job's workspace and are not
+ * reported by the engine: check inputs with the single-job API first.  An engine is used
+ * from one host thread at a time.
+ * ------------------------------------------------------------------------------------- */
+typedef enum { FWI_JOB_MODEL = 0, FWI_JOB_BORN = 1, FWI_JOB_GRADIENT = 2 } fwi_job_kind;
+
+typedef struct {
+    fwi_job_kind kind;
+    fwi_grid grid;
+    fwi_param pz;
+    const float *xi_a, *xi_b;      /* [nz][nx] contrasts (device) */
+    const float *dxi_a, *dxi_b;    /* BORN: [nz][nx] perturbation (device) */
+    fwi_sources src;               /* device pointers, as for fwi_model */
+    fwi_receivers rec;
+    float *traces;                 /* MODEL, BORN: [ns][nr][nt] output (device) */
+    const float *data;             /* GRADIENT: [ns][nr][nt] observed traces (device) */
+    double *misfit;                /* GRADIENT: 1 float64 output (device) */
+    double *grads;                 /* GRADIENT: [5][2][nz][nx] float64 output (device) */
+    size_t work_budget;            /* the job runs the plan fwi_workspace_bytes(grid, ns, nr, op,
+                                      work_budget) gives (0: the smallest plan) */
+} fwi_job;
+
+typedef struct fwi_engine fwi_engine;
+
+/* Creates an engine over `arena` (device, arena_bytes, 256-byte aligned) and `stream`. */
+int fwi_engine_create(fwi_engine **engine, void *arena, size_t arena_bytes, void *stream);
+
+/* Validates and queues a copy of *job; *ticket receives its id (1, 2, ...).  FWI_EINVAL for
+ * invalid arguments, FWI_ENOMEM when the job's workspace exceeds the arena. */
+int fwi_engine_submit(fwi_engine *engine, const fwi_job *job, long long *ticket);
+
+/* Runs up to `iterations` engine iterations (admission, one time step of every running job,
+ * retirement), enqueued on the engine's stream without waiting for the GPU.  Writes to
+ * done[0 .. *ndone) the tickets (at most max_done per call; the rest come back on later
+ * calls) of jobs whose results are complete on the device.  When no job is left queued or
+ * running, the call waits for the GPU to finish the outstanding ones. */
+int fwi_engine_run(fwi_engine *engine, int iterations, long long *done, int max_done, int *ndone);
+
+/* Jobs queued, running (admitted, not retired) and retired but not yet reported as done;
+ * bytes of the arena in use. */
+int fwi_engine_info(fwi_engine *engine, int *queued, int *running, int *pending, size_t *arena_used);
+
+/* Waits for the engine's stream and frees the engine (not the arena). */
+int fwi_engine_destroy(fwi_engine *engine);
 
 /* Per-launch timing (no counterpart in the paper: measurement support).  While enabled,
  * every kernel launch of the library is bracketed by a CUDA event pair recorded on the

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -79,6 +80,8 @@ Profiler g_prof;
 // Launch-shape overrides set by fwi_set_tile (0: built-in defaults); read when a plan is made.
 int g_tile_tz = 0;
 int g_tile_variant = 0;
+// Checkpoint interval forced by fwi_set_checkpoint (0: the planner chooses).
+int g_ckpt_every = 0;
 
 constexpr size_t ALIGN = 256;
 constexpr int RED_BLOCKS = 264;   // misfit partial sums per shot group
@@ -106,12 +109,11 @@ struct Plan {
     size_t total = 0;
 };
 
-constexpr int MAX_NX = 1536;   // computational columns: one streaming CTA of <= 384 threads spans a row
-
+// The time-step kernels address a shot's field with 32-bit offsets: Px * Nz < 2^31.
 bool grid_ok(const fwi_grid *g)
 {
     return g && g->nx >= 2 && g->nz >= 2 && g->sponge >= 0 && (g->order == 4 || g->order == 8) &&
-           g->nx + 2 * g->sponge <= MAX_NX &&
+           (long long)(((g->nx + 2LL * g->sponge + 31) / 32) * 32) * (g->nz + 2LL * g->sponge) < (1LL << 31) &&
            g->nt >= 1 && g->dx > 0 && g->dt > 0 && g->vp_o > 0 && g->rho_o > 0 &&
            std::isfinite(g->dx) && std::isfinite(g->dt);
 }
@@ -190,6 +192,17 @@ bool make_plan(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, size_t bud
     Plan tmp;
     layout(tmp, g, op, ns, nr, 1, nt);
     const long long Np = tmp.d.Np;
+    if (g_ckpt_every > 0 && g_ckpt_every < nt) {
+        // checkpoints every g_ckpt_every steps, as many shots per group as fit
+        layout(P, g, op, ns, nr, 1, g_ckpt_every);
+        if (budget == 0) return true;
+        if (P.total > budget) return false;
+        for (int B = nsm; B >= 1; --B) {
+            layout(P, g, op, ns, nr, B, g_ckpt_every);
+            if (P.total <= budget) return true;
+        }
+        return false;
+    }
     const int Cs = std::max(1, (int)std::ceil(std::sqrt(3.0 * nt)));
     // minimum: one shot, whichever history scheme is smaller
     Plan a, b;
@@ -218,8 +231,8 @@ int check_common(const fwi_grid *g, const float *xa, const float *xb, const fwi_
                  const fwi_receivers *rec, void *work, size_t work_bytes)
 {
     if (!grid_ok(g))
-        return fail(FWI_EINVAL, "invalid grid (nx, nz >= 2, nx + 2 sponge <= %d, order 4 or 8, nt >= 1, "
-                                "dx, dt, vp_o, rho_o > 0)", MAX_NX);
+        return fail(FWI_EINVAL, "invalid grid (nx, nz >= 2, fewer than 2^31 padded cells per shot, order 4 or 8, "
+                                "nt >= 1, dx, dt, vp_o, rho_o > 0)");
     if (!xa || !xb) return fail(FWI_EINVAL, "null contrast pointer");
     if (!src || !rec || src->ns < 0 || rec->nr < 0) return fail(FWI_EINVAL, "invalid sources/receivers");
     if (src->ns > 0 && (!src->xy || !src->wavelet)) return fail(FWI_EINVAL, "null source arrays");
@@ -307,18 +320,18 @@ struct Fwd {
         const float *vx0 = at<float>(work, P.vx[n & 1]), *vz0 = at<float>(work, P.vz[n & 1]);
         float *vx1 = at<float>(work, P.vx[(n + 1) & 1]), *vz1 = at<float>(work, P.vz[(n + 1) & 1]);
         const dim3 grid = warp_grid(P, bg);
-        const fwi::Model mo = model_of(P, work);
+        const fwi::FwdArgs args{p0, vx0, vz0, p1, vx1, vz1, model_of(P, work), d, P.st, src, n, P.tz, bg};
         if (P.M == 2) {
             switch (P.variant) {
-            case 1: LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
-            case 2: LAUNCH((fwi::k_fwd_warp<2, 6>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
-            default: LAUNCH((fwi::k_fwd_warp<2, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
+            case 1: LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, args); break;
+            case 2: LAUNCH((fwi::k_fwd_warp<2, 6>), grid, 64, 0, st, args); break;
+            default: LAUNCH((fwi::k_fwd_warp<2, 1>), grid, 64, 0, st, args);
             }
         } else {
             switch (P.variant) {
-            case 1: LAUNCH((fwi::k_fwd_warp<4, 8>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
-            case 2: LAUNCH((fwi::k_fwd_warp<4, 6>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg); break;
-            default: LAUNCH((fwi::k_fwd_warp<4, 1>), grid, 64, 0, st, p0, vx0, vz0, p1, vx1, vz1, mo, d, P.st, src, n, P.tz, bg);
+            case 1: LAUNCH((fwi::k_fwd_warp<4, 8>), grid, 64, 0, st, args); break;
+            case 2: LAUNCH((fwi::k_fwd_warp<4, 6>), grid, 64, 0, st, args); break;
+            default: LAUNCH((fwi::k_fwd_warp<4, 1>), grid, 64, 0, st, args);
             }
         }
     }
@@ -415,7 +428,7 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
             const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
             float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
             const dim3 grid = warp_grid(P, bg, 1);
-#define ADJ_ARGS ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, P.tz, bg
+#define ADJ_ARGS fwi::AdjArgs{ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, P.tz, bg}
             if (P.M == 2) {
                 switch (P.variant) {
                 case 1: LAUNCH((fwi::k_adj_warp<2, 8>), grid, 32, 0, st, ADJ_ARGS); break;
@@ -499,6 +512,8 @@ namespace fwi_internal {
 void set_error(const char *msg) { g_err = msg ? msg : ""; }
 }
 
+#include "fwi_engine.inc"
+
 extern "C" {
 
 size_t fwi_workspace_bytes(const fwi_grid *g, int ns, int nr, fwi_op op, size_t budget_bytes)
@@ -564,8 +579,8 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
             auto F = [&](const size_t *a) { return at<float>(work, a[i]); };
             auto G = [&](const size_t *a) { return at<float>(work, a[o]); };
             const dim3 grid = warp_grid(P, bg, 1);
-#define BORN_ARGS F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), G(P.vz), G(P.dp), \
-                  G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz, bg
+#define BORN_ARGS fwi::BornArgs{F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), \
+                  G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz, bg}
             if (P.M == 2) {
                 if (P.variant == 2) LAUNCH((fwi::k_born_warp<2, 12>), grid, 32, 0, st, BORN_ARGS);
                 else LAUNCH((fwi::k_born_warp<2, 1>), grid, 32, 0, st, BORN_ARGS);
@@ -629,6 +644,14 @@ int fwi_status(void *work, void *stream)
 }
 
 const char *fwi_last_error(void) { return g_err.c_str(); }
+
+
+int fwi_set_checkpoint(int every)
+{
+    if (every < 0) return fail(FWI_EINVAL, "checkpoint interval must be >= 0");
+    g_ckpt_every = every;
+    return FWI_OK;
+}
 
 int fwi_set_tile(int tz, int variant)
 {

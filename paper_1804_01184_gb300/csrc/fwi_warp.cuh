@@ -30,18 +30,50 @@ struct Strip {
     int x0, z0, s;      // strip origin and shot
 };
 
-// warp -> strip; the shot varies fastest so that warps running together stream the same model
-// rows (shared by every shot of the launch) and find them in L1/L2
-__device__ __forceinline__ Strip strip_of(const Dims &d, int tz, int nshots, int wpb, bool &valid)
+// Warps a launch over `nshots` shots of grid d needs.
+__host__ __device__ __forceinline__ int strip_warps(const Dims &d, int tz, int nshots)
 {
-    const int w = blockIdx.x * wpb + (threadIdx.x >> 5);
-    const int nxs = (d.Nx + WS - 1) / WS, nzs = (d.Nz + tz - 1) / tz;
-    valid = w < nxs * nzs * nshots;
+    return ((d.Nx + WS - 1) / WS) * ((d.Nz + tz - 1) / tz) * nshots;
+}
+
+// warp w of a launch -> strip; the shot varies fastest so that warps running together stream
+// the same model rows (shared by every shot of the launch) and find them in L1/L2
+__device__ __forceinline__ Strip strip_at(int w, const Dims &d, int tz, int nshots, bool &valid)
+{
+    const int nxs = (d.Nx + WS - 1) / WS;
+    valid = w < strip_warps(d, tz, nshots);
     Strip st;
     st.s = w % nshots;
     st.x0 = ((w / nshots) % nxs) * WS;
     st.z0 = (w / (nshots * nxs)) * tz;
     return st;
+}
+
+__device__ __forceinline__ Strip strip_of(const Dims &d, int tz, int nshots, int wpb, bool &valid)
+{
+    return strip_at(blockIdx.x * wpb + (threadIdx.x >> 5), d, tz, nshots, valid);
+}
+
+// Batched launches carry their job table as a kernel parameter (__grid_constant__, at most
+// 32 KB): warp (or thread) w belongs to job j with wstart[j] <= w < wstart[j+1].
+constexpr int BATCH_CAP = 96;
+
+template <typename A>
+struct BatchTable {
+    int njobs;
+    int wstart[BATCH_CAP + 1];
+    A jobs[BATCH_CAP];
+};
+
+__device__ __forceinline__ int job_of(int w, const int *wstart, int njobs, int &local)
+{
+    int lo = 0, hi = njobs;          // invariant: wstart[lo] <= w < wstart[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (wstart[mid] <= w) lo = mid; else hi = mid;
+    }
+    local = w - wstart[lo];
+    return lo;
 }
 
 // Role of a lane: its main float4 (own column, or the halo float4 for lanes 30/31) and, on the
@@ -103,30 +135,42 @@ __device__ __forceinline__ float4 ldg_if(const float *p, bool v) { return v ? ld
 // ------------------------------------------------------------------ forward step (S3)
 //
 //   v^{n+1/2} = d_v (v^{n-1/2} - dt b D+ p^n);  p^{n+1} = d_p (p^n - dt K D-.v^{n+1/2}) + dt K w_n beta/dx^2
-template <int M, int MINB>
-__global__ void __launch_bounds__(64, MINB) k_fwd_warp(const float *__restrict__ p0, const float *__restrict__ vx0,
-                                                      const float *__restrict__ vz0, float *__restrict__ p1,
-                                                      float *__restrict__ vx1, float *__restrict__ vz1, Model mo,
-                                                      Dims d, Stencil st, Source src, int n, int tz, int nshots)
+struct FwdArgs {
+    const float *p0, *vx0, *vz0;    // p^n, v^{n-1/2} of the launch's shots
+    float *p1, *vx1, *vz1;          // p^{n+1}, v^{n+1/2}
+    Model mo;
+    Dims d;
+    Stencil st;
+    Source src;                     // sources of the launch's shots
+    int n, tz, nshots;
+};
+
+// Shared memory of one warp of a forward launch.
+struct FwdSmem {
+    float ring[WRP][WROW];          // p^n rows
+    float stg[WNS][5][WROW];        // vz, bz (row f-M); vx, bx, K (row j)
+    float vxr[2][WROW];             // v_x^{n+1/2} rows
+};
+
+template <int M>
+__device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdSmem &sh)
 {
     constexpr int R = 2 * M;
-    __shared__ __align__(16) float sring[2][WRP][WROW];     // p^n rows
-    __shared__ __align__(16) float sstg[2][WNS][5][WROW];   // vz, bz (row f-M); vx, bx, K (row j)
-    __shared__ __align__(16) float svx[2][2][WROW];         // v_x^{n+1/2} rows
-    bool valid;
-    const Strip sp = strip_of(d, tz, nshots, 2, valid);
-    if (!valid) return;
-    const int wid = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
-    float(*ring)[WROW] = sring[wid];
-    float(*stg)[5][WROW] = sstg[wid];
-    float(*vxr)[WROW] = svx[wid];
+    const Dims &d = a.d;
+    const Model &mo = a.mo;
+    const Stencil &st = a.st;
+    const int n = a.n, tz = a.tz;
+    const int lane = threadIdx.x & 31;
+    float(*ring)[WROW] = sh.ring;
+    float(*stg)[5][WROW] = sh.stg;
+    float(*vxr)[WROW] = sh.vxr;
     const LaneMap L = lane_map(lane, sp.x0, d);
     for (int k = lane; k < 2 * WROW; k += 32) (&vxr[0][0])[k] = 0.f;
     const long long so = (long long)sp.s * d.Np;
-    const float *P0 = p0 + so, *VX0 = vx0 + so, *VZ0 = vz0 + so;
-    float *P1 = p1 + so, *VX1 = vx1 + so, *VZ1 = vz1 + so;
-    const SrcCells sc = src_cells(src, sp.s, d.Px);
-    const float wn = __ldg(src.wav + n);
+    const float *P0 = a.p0 + so, *VX0 = a.vx0 + so, *VZ0 = a.vz0 + so;
+    float *P1 = a.p1 + so, *VX1 = a.vx1 + so, *VZ1 = a.vz1 + so;
+    const SrcCells sc = src_cells(a.src, sp.s, d.Px);
+    const float wn = __ldg(a.src.wav + n);
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
     const bool hsrc = strip_has_src(sc, sp.x0, z0, zend);
@@ -202,6 +246,31 @@ __global__ void __launch_bounds__(64, MINB) k_fwd_warp(const float *__restrict__
     cp_wait<0>();
 }
 
+template <int M, int MINB>
+__global__ void __launch_bounds__(64, MINB) k_fwd_warp(FwdArgs a)
+{
+    __shared__ __align__(16) FwdSmem sh[2];
+    bool valid;
+    const Strip sp = strip_of(a.d, a.tz, a.nshots, 2, valid);
+    if (!valid) return;
+    fwd_body<M>(a, sp, sh[(threadIdx.x >> 5) & 1]);
+}
+
+// One time step of several independent jobs: warp w runs strip (w - wstart[j]) of job j.
+template <int M>
+__global__ void __launch_bounds__(64) k_fwd_batch(const __grid_constant__ BatchTable<FwdArgs> t)
+{
+    __shared__ __align__(16) FwdSmem sh[2];
+    const int w = blockIdx.x * 2 + (threadIdx.x >> 5);
+    if (w >= t.wstart[t.njobs]) return;
+    int local;
+    const FwdArgs &a = t.jobs[job_of(w, t.wstart, t.njobs, local)];
+    bool valid;
+    const Strip sp = strip_at(local, a.d, a.tz, a.nshots, valid);
+    if (!valid) return;
+    fwd_body<M>(a, sp, sh[(threadIdx.x >> 5) & 1]);
+}
+
 // ------------------------------------------------------------- adjoint step (S7)
 //
 // Reverse step n, the transpose of k_fwd_warp's step, with the cross-correlation fused in:
@@ -211,30 +280,45 @@ __global__ void __launch_bounds__(64, MINB) k_fwd_warp(const float *__restrict__
 // The last line pairs each pressure adjoint with its own snapshot one launch earlier than the
 // textbook form sum pbar^{n+1} (p^{n+1} - d_p p^n); the receiver-cell remainder
 // (R^T r_n) p^{n+1} is added by k_adj_inject_k.
-template <int M, int MINB>
-__global__ void __launch_bounds__(32, 2 * MINB) k_adj_warp(const float *__restrict__ ap0, const float *__restrict__ avx0,
-                                                          const float *__restrict__ avz0, float *__restrict__ ap1,
-                                                          float *__restrict__ avx1, float *__restrict__ avz1, Model mo,
-                                                          const float *__restrict__ pn, float *__restrict__ accK,
-                                                          float *__restrict__ accBx, float *__restrict__ accBz, Dims d,
-                                                          Stencil st, int tz, int nshots)
+struct AdjArgs {
+    const float *ap0, *avx0, *avz0;   // pbar^{n+1} (after injection), vbar^{n+1/2}
+    float *ap1, *avx1, *avz1;         // pbar^n, new vbar
+    Model mo;
+    const float *pn;                  // p^n snapshots of the launch's shots
+    float *accK, *accBx, *accBz;      // FP32 gradient accumulators of the launch's shots
+    Dims d;
+    Stencil st;
+    int tz, nshots;
+};
+
+// Shared memory of one adjoint warp.
+struct AdjSmem {
+    float pr[WRP][WROW];              // p^n rows
+    float qr[8][WROW];                // K d_p pbar^{n+1} rows (2M <= 8)
+    float stg[WNS][7][WROW];          // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
+    float bur[2][WROW];               // bx u_x rows
+};
+
+template <int M>
+__device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjSmem &sh)
 {
     constexpr int R = 2 * M, NF = 7;
-    // one warp per block
-    __shared__ __align__(16) float pr[WRP][WROW];      // p^n rows
-    __shared__ __align__(16) float qr[R][WROW];        // K d_p pbar^{n+1} rows
-    __shared__ __align__(16) float stg[WNS][NF][WROW]; // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
-    __shared__ __align__(16) float bur[2][WROW];       // bx u_x rows
-    bool valid;
-    const Strip sp = strip_of(d, tz, nshots, 1, valid);
-    if (!valid) return;
+    const Dims &d = a.d;
+    const Model &mo = a.mo;
+    const Stencil &st = a.st;
+    const int tz = a.tz;
+    float(*pr)[WROW] = sh.pr;
+    float(*qr)[WROW] = sh.qr;
+    float(*stg)[NF][WROW] = sh.stg;
+    float(*bur)[WROW] = sh.bur;
     const int lane = threadIdx.x & 31;
     const LaneMap L = lane_map(lane, sp.x0, d);
     for (int k = lane; k < R * WROW; k += 32) (&qr[0][0])[k] = 0.f;
     for (int k = lane; k < 2 * WROW; k += 32) (&bur[0][0])[k] = 0.f;
     const long long so = (long long)sp.s * d.Np;
-    const float *A0 = ap0 + so, *AX0 = avx0 + so, *AZ0 = avz0 + so, *PN = pn + so;
-    float *A1 = ap1 + so, *AX1 = avx1 + so, *AZ1 = avz1 + so, *GK = accK + so, *GX = accBx + so, *GZ = accBz + so;
+    const float *A0 = a.ap0 + so, *AX0 = a.avx0 + so, *AZ0 = a.avz0 + so, *PN = a.pn + so;
+    float *A1 = a.ap1 + so, *AX1 = a.avx1 + so, *AZ1 = a.avz1 + so;
+    float *GK = a.accK + so, *GX = a.accBx + so, *GZ = a.accBz + so;
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const float4 axe = ldg_if(mo.ax + L.ec, L.ein);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
@@ -328,6 +412,30 @@ __global__ void __launch_bounds__(32, 2 * MINB) k_adj_warp(const float *__restri
     cp_wait<0>();
 }
 
+template <int M, int MINB>
+__global__ void __launch_bounds__(32, 2 * MINB) k_adj_warp(AdjArgs a)
+{
+    __shared__ __align__(16) AdjSmem sh;   // one warp per block
+    bool valid;
+    const Strip sp = strip_of(a.d, a.tz, a.nshots, 1, valid);
+    if (!valid) return;
+    adj_body<M>(a, sp, sh);
+}
+
+template <int M>
+__global__ void __launch_bounds__(32) k_adj_batch(const __grid_constant__ BatchTable<AdjArgs> t)
+{
+    __shared__ __align__(16) AdjSmem sh;
+    const int w = blockIdx.x;
+    if (w >= t.wstart[t.njobs]) return;
+    int local;
+    const AdjArgs &a = t.jobs[job_of(w, t.wstart, t.njobs, local)];
+    bool valid;
+    const Strip sp = strip_at(local, a.d, a.tz, a.nshots, valid);
+    if (!valid) return;
+    adj_body<M>(a, sp, sh);
+}
+
 // pbar^{n+1} += R^T r_n at the receivers, and the receiver-cell part of the K-gradient,
 // accK += (R^T r_n) p^{n+1} (see k_adj_warp).  One thread per shot and receiver.
 __global__ void k_adj_inject_k(float *__restrict__ ap, float *__restrict__ accK, const float *__restrict__ pn1,
@@ -353,33 +461,49 @@ __global__ void k_adj_inject_k(float *__restrict__ ap, float *__restrict__ accK,
 // Background (p, v) and scattered (q, u) fields stepped together:
 //   u^{n+1/2} = d_v (u^{n-1/2} - dt b D+ q^n - dt db D+ p^n)
 //   q^{n+1}   = d_p (q^n - dt K D-.u^{n+1/2} - dt dK D-.v^{n+1/2}) + dt dK w_n beta / dx^2
-template <int M, int MINB>
-__global__ void __launch_bounds__(32, MINB) k_born_warp(const float *__restrict__ p0, const float *__restrict__ vx0,
-                                                       const float *__restrict__ vz0, const float *__restrict__ q0,
-                                                       const float *__restrict__ ux0, const float *__restrict__ uz0,
-                                                       float *__restrict__ p1, float *__restrict__ vx1,
-                                                       float *__restrict__ vz1, float *__restrict__ q1,
-                                                       float *__restrict__ ux1, float *__restrict__ uz1, Model mo,
-                                                       Pert pe, Dims d, Stencil st, Source src, int n, int tz,
-                                                       int nshots)
+struct BornArgs {
+    const float *p0, *vx0, *vz0, *q0, *ux0, *uz0;   // background and scattered state at step n
+    float *p1, *vx1, *vz1, *q1, *ux1, *uz1;         // ... at step n+1
+    Model mo;
+    Pert pe;
+    Dims d;
+    Stencil st;
+    Source src;
+    int n, tz, nshots;
+};
+
+struct BornSmem {
+    float pr[WRP][WROW];
+    float qr[WRP][WROW];
+    float stg[WPD + 1][10][WROW];
+    float vr[2][WROW];
+    float ur[2][WROW];
+};
+
+template <int M>
+__device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, BornSmem &sh)
 {
     constexpr int R = 2 * M, NS = WPD + 1, NF = 10;
-    __shared__ __align__(16) float spr[WRP][WROW];
-    __shared__ __align__(16) float sqr[WRP][WROW];
-    __shared__ __align__(16) float stg[NS][NF][WROW];
-    __shared__ __align__(16) float svr[2][WROW];
-    __shared__ __align__(16) float sur[2][WROW];
-    bool valid;
-    const Strip sp = strip_of(d, tz, nshots, 1, valid);
-    if (!valid) return;
+    const Dims &d = a.d;
+    const Model &mo = a.mo;
+    const Pert &pe = a.pe;
+    const Stencil &st = a.st;
+    const int n = a.n, tz = a.tz;
+    float(*spr)[WROW] = sh.pr;
+    float(*sqr)[WROW] = sh.qr;
+    float(*stg)[NF][WROW] = sh.stg;
+    float(*svr)[WROW] = sh.vr;
+    float(*sur)[WROW] = sh.ur;
     const int lane = threadIdx.x & 31;
     const LaneMap L = lane_map(lane, sp.x0, d);
     for (int k = lane; k < 2 * WROW; k += 32) { (&svr[0][0])[k] = 0.f; (&sur[0][0])[k] = 0.f; }
     const long long so = (long long)sp.s * d.Np;
-    const float *P0 = p0 + so, *VX0 = vx0 + so, *VZ0 = vz0 + so, *Q0 = q0 + so, *UX0 = ux0 + so, *UZ0 = uz0 + so;
-    float *P1 = p1 + so, *VX1 = vx1 + so, *VZ1 = vz1 + so, *Q1 = q1 + so, *UX1 = ux1 + so, *UZ1 = uz1 + so;
-    const SrcCells sc = src_cells(src, sp.s, d.Px);
-    const float wn = __ldg(src.wav + n);
+    const float *P0 = a.p0 + so, *VX0 = a.vx0 + so, *VZ0 = a.vz0 + so;
+    const float *Q0 = a.q0 + so, *UX0 = a.ux0 + so, *UZ0 = a.uz0 + so;
+    float *P1 = a.p1 + so, *VX1 = a.vx1 + so, *VZ1 = a.vz1 + so;
+    float *Q1 = a.q1 + so, *UX1 = a.ux1 + so, *UZ1 = a.uz1 + so;
+    const SrcCells sc = src_cells(a.src, sp.s, d.Px);
+    const float wn = __ldg(a.src.wav + n);
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
     const bool hsrc = strip_has_src(sc, sp.x0, z0, zend);
@@ -484,5 +608,33 @@ __global__ void __launch_bounds__(32, MINB) k_born_warp(const float *__restrict_
     }
     cp_wait<0>();
 }
+
+template <int M, int MINB>
+__global__ void __launch_bounds__(32, MINB) k_born_warp(BornArgs a)
+{
+    __shared__ __align__(16) BornSmem sh;
+    bool valid;
+    const Strip sp = strip_of(a.d, a.tz, a.nshots, 1, valid);
+    if (!valid) return;
+    born_body<M>(a, sp, sh);
+}
+
+template <int M>
+__global__ void __launch_bounds__(32) k_born_batch(const __grid_constant__ BatchTable<BornArgs> t)
+{
+    __shared__ __align__(16) BornSmem sh;
+    const int w = blockIdx.x;
+    if (w >= t.wstart[t.njobs]) return;
+    int local;
+    const BornArgs &a = t.jobs[job_of(w, t.wstart, t.njobs, local)];
+    bool valid;
+    const Strip sp = strip_at(local, a.d, a.tz, a.nshots, valid);
+    if (!valid) return;
+    born_body<M>(a, sp, sh);
+}
+
+static_assert(sizeof(BatchTable<FwdArgs>) <= 32000 && sizeof(BatchTable<AdjArgs>) <= 32000 &&
+                  sizeof(BatchTable<BornArgs>) <= 32000,
+              "batch table exceeds the kernel parameter space");
 
 }  // namespace fwi

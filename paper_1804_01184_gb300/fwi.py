@@ -78,6 +78,7 @@ def lib():
             L.fwi_last_error.restype = C.c_char_p
             L.fwi_launch_count.restype = C.c_longlong
             L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
+            L.fwi_set_checkpoint.argtypes = [C.c_int]
             L.fwi_model_noalloc.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp]
             L.fwi_profile.argtypes = [C.c_int]
             L.fwi_profile_report.argtypes = [C.c_char_p, C.c_size_t]
@@ -135,6 +136,11 @@ def fwi_status(work: torch.Tensor, stream=None):
 def fwi_set_tile(tz: int = 0, variant: int = 0):
     """Launch-shape override for plans made afterwards (0, 0 = built-in defaults)."""
     _raise(lib().fwi_set_tile(int(tz), int(variant)))
+
+
+def fwi_set_checkpoint(every: int = 0):
+    """Checkpoint interval for gradient plans made afterwards (0 = the planner chooses)."""
+    _raise(lib().fwi_set_checkpoint(int(every)))
 
 
 def launch_count() -> int:

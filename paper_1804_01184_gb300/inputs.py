@@ -18,6 +18,10 @@ experiments, Sec. "Almost Well-posed Example" and the scatterer table):
     amplitude in [-0.5, 0.5] (vp-rho contrasts).
   * ``config_paper`` -- the paper's own acquisition: 10 sources, 100 receivers, 490 m
     circle, 5 Hz Ricker, vp = 2000 m/s, rho = 2000 kg/m^3, Gaussian sigma 50 m.
+  * ``config_smooth`` -- 1201 x 1201, dx 2.5 m, dt 0.25 ms, 6000 steps, 16 sources / 256
+    receivers on a 1200 m circle; smooth random background (seeded normal fields, Gaussian
+    filter sigma 50 cells, min-max scaled to vp 1500-3500 m/s and rho 1000-2500 kg/m^3) plus
+    4 Gaussian anomalies (sigma 25 m, +-20 % in vp and rho, centres in a 600 m disc).
   * ``small_case`` -- seeded random heterogeneous models on small grids for parity tests.
 """
 from __future__ import annotations
@@ -155,6 +159,34 @@ def config_paper(nt=1400, which="vp", amplitude=0.2):
     return Workload("paper-121x121-o8", n, n, dx, 1e-3, nt, 8, 40, 2000.0, 2000.0, PZ_VP_RHO,
                     xa, xb, circle(10, 490.0, c), circle(100, 490.0, c, 0.5),
                     ricker(nt, 1e-3, 5.0))
+
+
+def config_smooth(nt=6000, ns=16, nr=256, n=1201, seed_vp=3, seed_rho=4, seed_anom=5):
+    """Differentiation workload (vp-rho contrasts relative to vp_o = rho_o = 2000).  Returns the
+    workload of the true model (background + anomalies) and the background contrasts."""
+    from scipy.ndimage import gaussian_filter
+    dx = 2.5
+    c = centre_of(n, n, dx)
+
+    def field(seed, lo, hi):
+        f = gaussian_filter(np.random.default_rng(seed).standard_normal((n, n)), 50.0, mode="reflect")
+        f = (f - f.min()) / (f.max() - f.min())
+        return lo + (hi - lo) * f
+
+    vp_bg, rho_bg = field(seed_vp, 1500.0, 3500.0), field(seed_rho, 1000.0, 2500.0)
+    rng = np.random.default_rng(seed_anom)
+    avp, arho = np.zeros((n, n)), np.zeros((n, n))
+    for _ in range(4):
+        r, th = 600.0 * np.sqrt(rng.random()), 2 * math.pi * rng.random()
+        g = gaussian(n, n, dx, (c[0] + r * math.cos(th), c[1] + r * math.sin(th)), 25.0).astype(np.float64)
+        avp += rng.uniform(-0.2, 0.2) * g
+        arho += rng.uniform(-0.2, 0.2) * g
+    vp, rho = vp_bg * (1 + avp), rho_bg * (1 + arho)
+    w = Workload(f"smooth-{n}x{n}-o8", n, n, dx, 2.5e-4, nt, 8, 40, 2000.0, 2000.0, PZ_VP_RHO,
+                 (vp / 2000.0 - 1).astype(np.float32), (rho / 2000.0 - 1).astype(np.float32),
+                 circle(ns, 1200.0, c), circle(nr, 1200.0, c, 0.5), ricker(nt, 2.5e-4, 15.0),
+                 sponge_v=4200.0)
+    return w, ((vp_bg / 2000.0 - 1).astype(np.float32), (rho_bg / 2000.0 - 1).astype(np.float32))
 
 
 def small_case(seed=0, nx=45, nz=37, nt=120, order=8, sponge=6, ns=3, nr=7, pz=PZ_VP_RHO,

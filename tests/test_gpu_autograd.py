@@ -80,3 +80,36 @@ def test_checkpointed_history_gives_same_gradient(A):
         grads.append((a.grad.cpu().numpy(), b.grad.cpu().numpy()))
     for k in range(2):
         assert rel_l2(grads[1][k], grads[0][k]) <= 1e-6
+
+
+def test_config_smooth_taylor_with_checkpoints(A):
+    """Full differentiation workload: 1201 x 1201 (+40-cell sponge), 6000 steps, 16 shots,
+    smooth random background + 4 anomalies; checkpoints every 200 steps with recomputation;
+    Taylor test at 6 step sizes through torch.autograd."""
+    from paper_1804_01184_gb300 import fwi
+    w, (a_bg, b_bg) = I.config_smooth()
+    g = gpu_grid(w)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    src, rec, wav = dev(w.src_xy), dev(w.rec_xy), dev(w.wavelet)
+    data = fwi.fwi_model(g, w.pz, dev(w.xi_a), dev(w.xi_b), src, wav, rec)
+    fwi.fwi_set_checkpoint(200)
+    try:
+        a0 = dev(a_bg).requires_grad_()
+        b0 = dev(b_bg).requires_grad_()
+        tr = A.model(a0, b0, g, w.pz, src, wav, rec)
+        J0 = 0.5 * ((tr.double() - data.double()) ** 2).sum()
+        J0.backward()
+    finally:
+        fwi.fwi_set_checkpoint(0)
+    assert torch.isfinite(a0.grad).all() and torch.isfinite(b0.grad).all()
+    da, db = dev(w.xi_a - a_bg), dev(w.xi_b - b_bg)          # towards the true model
+    lin = (a0.grad.double() * da.double()).sum() + (b0.grad.double() * db.double()).sum()
+    assert lin.item() < 0                                      # a descent direction
+    rem = []
+    with torch.no_grad():
+        for h in [0.2 / 2 ** k for k in range(6)]:
+            trh = fwi.fwi_model(g, w.pz, a0 + h * da, b0 + h * db, src, wav, rec)
+            Jh = 0.5 * ((trh.double() - data.double()) ** 2).sum()
+            rem.append(abs((Jh - J0 - h * lin).item()))
+    slopes = np.log2(np.array(rem[:-1]) / np.array(rem[1:]))
+    assert np.all(slopes[:3] > 1.7) and np.all(slopes[:3] < 2.3), slopes
