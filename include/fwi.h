@@ -229,7 +229,10 @@ int fwi_engine_submit(fwi_engine *engine, const fwi_job *job, long long *ticket)
  * retirement), enqueued on the engine's stream without waiting for the GPU.  Writes to
  * done[0 .. *ndone) the tickets (at most max_done per call; the rest come back on later
  * calls) of jobs whose results are complete on the device.  When no job is left queued or
- * running, the call waits for the GPU to finish the outstanding ones. */
+ * running, the call waits for the GPU to finish the outstanding ones.  A call first waits
+ * for the GPU to finish the work of the call before the previous one, so the host never
+ * runs more than one call's iterations ahead of the GPU (what bounds the wait of a job
+ * submitted between calls). */
 int fwi_engine_run(fwi_engine *engine, int iterations, long long *done, int max_done, int *ndone);
 
 /* Jobs queued, running (admitted, not retired) and retired but not yet reported as done;

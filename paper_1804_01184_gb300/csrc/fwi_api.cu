@@ -100,7 +100,7 @@ struct Plan {
     int variant = 0;  // kernel variant (register budget) chosen by the tuner
     // byte offsets into the workspace
     size_t status = 0, K = 0, bx = 0, bz = 0, ax = 0, axh = 0, az = 0, azh = 0;
-    size_t sidx = 0, sw = 0, ridx = 0, rw = 0;
+    size_t sidx = 0, sw = 0, ridx = 0, rw = 0, rl = 0;
     size_t p[2] = {0, 0}, vx[2] = {0, 0}, vz[2] = {0, 0};          // ping-pong state
     size_t dK = 0, dbx = 0, dbz = 0, dp[2] = {0, 0}, dvx[2] = {0, 0}, dvz[2] = {0, 0};
     size_t ap[2] = {0, 0}, avx[2] = {0, 0}, avz[2] = {0, 0};
@@ -153,6 +153,7 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
     P.sw = take(4 * (size_t)std::max(ns, 1) * F);
     P.ridx = take(4 * (size_t)std::max(nr, 1) * sizeof(long long));
     P.rw = take(4 * (size_t)std::max(nr, 1) * F);
+    P.rl = take(4 * (size_t)std::max(nr, 1) * sizeof(int));
     for (int b = 0; b < 2; ++b) { P.p[b] = take(bfield); P.vx[b] = take(bfield); P.vz[b] = take(bfield); }
     if (op == FWI_OP_BORN) {
         P.dK = take(field); P.dbx = take(field); P.dbz = take(field);
@@ -237,6 +238,8 @@ int check_common(const fwi_grid *g, const float *xa, const float *xb, const fwi_
     if (!src || !rec || src->ns < 0 || rec->nr < 0) return fail(FWI_EINVAL, "invalid sources/receivers");
     if (src->ns > 0 && (!src->xy || !src->wavelet)) return fail(FWI_EINVAL, "null source arrays");
     if (rec->nr > 0 && !rec->xy) return fail(FWI_EINVAL, "null receiver array");
+    if (src->ns > (1 << 20) || rec->nr > (1 << 20) || (long long)src->ns * rec->nr > (1LL << 28))
+        return fail(FWI_EINVAL, "too many sources or receivers (at most 2^20 each, 2^28 traces)");
     if (!work) return fail(FWI_EINVAL, "null workspace");
     if (reinterpret_cast<uintptr_t>(work) % ALIGN) return fail(FWI_EINVAL, "workspace not 256-byte aligned");
     (void)work_bytes;
@@ -286,9 +289,12 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
     if (src->ns > 0)
         LAUNCH(fwi::k_geometry, (src->ns + 127) / 128, 128, 0, st, src->xy, src->ns, d, g->dx,
                g->dt / (g->dx * g->dx), at<long long>(work, P.sidx), at<float>(work, P.sw), status);
-    if (rec->nr > 0)
+    if (rec->nr > 0) {
         LAUNCH(fwi::k_geometry, (rec->nr + 127) / 128, 128, 0, st, rec->xy, rec->nr, d, g->dx, 1.0,
                at<long long>(work, P.ridx), at<float>(work, P.rw), status);
+        LAUNCH(fwi::k_receiver_chain, (4 * rec->nr + 127) / 128, 128, 0, st, at<long long>(work, P.ridx), 4 * rec->nr,
+               at<int>(work, P.rl));
+    }
     return FWI_OK;
 }
 
@@ -423,8 +429,8 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
             float *ap0 = at<float>(work, P.ap[i]);
             const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
             if (P.nr > 0)
-                LAUNCH(fwi::k_adj_inject_k, (bg * P.nr + 127) / 128, 128, 0, st, ap0, aK, pn1, bg, P.nr, P.nt, n, d.Np,
-                       at<long long>(work, P.ridx), at<float>(work, P.rw), res);
+                LAUNCH(fwi::k_adj_inject_k, (bg * 4 * P.nr + 127) / 128, 128, 0, st, ap0, aK, pn1, bg, P.nr, P.nt, n,
+                       d.Np, at<long long>(work, P.ridx), at<float>(work, P.rw), at<int>(work, P.rl), res);
             const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
             float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
             const dim3 grid = warp_grid(P, bg, 1);

@@ -176,6 +176,24 @@ __global__ void k_geometry(const float *__restrict__ xy, int n, Dims d, double d
     idx[4 * k + 3] = cell(d, i0 + 1, j0 + 1);  w[4 * k + 3] = (float)(scale * tx * tz);
 }
 
+// Receiver footprints that share a cell, chained for a deterministic adjoint injection:
+// entry k (receiver k/4, corner k%4) gets the next entry with the same cell (n4 if none) in
+// bits 0..29, and bit 30 set when no earlier entry has its cell.  O(n4^2), run once.
+constexpr int CHAIN_FIRST = 1 << 30;
+
+__global__ void k_receiver_chain(const long long *__restrict__ idx, int n4, int *__restrict__ rl)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n4) return;
+    const long long c = idx[k];
+    bool first = true;
+    for (int m = 0; m < k && first; ++m) first = idx[m] != c;
+    int nx = n4;
+    for (int m = k + 1; m < n4; ++m)
+        if (idx[m] == c) { nx = m; break; }
+    rl[k] = nx | (first ? CHAIN_FIRST : 0);
+}
+
 // ------------------------------------------------------------ shared kernel arguments
 
 struct Model {

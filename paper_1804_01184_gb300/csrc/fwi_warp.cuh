@@ -438,22 +438,36 @@ __global__ void __launch_bounds__(32) k_adj_batch(const __grid_constant__ BatchT
 
 // pbar^{n+1} += R^T r_n at the receivers, and the receiver-cell part of the K-gradient,
 // accK += (R^T r_n) p^{n+1} (see k_adj_warp).  One thread per shot and receiver.
+// Injection of receiver footprint k of shot-slot s at step n: the first entry of every cell
+// sums the chain of footprints on that cell in receiver order and adds once, so the result
+// does not depend on thread order even when receivers share cells.
+__device__ __forceinline__ void inject_entry(float *__restrict__ ap, float *__restrict__ accK,
+                                             const float *__restrict__ pn1, int s, int k, int nr, int nt, int n,
+                                             long long Np, const long long *__restrict__ ridx,
+                                             const float *__restrict__ rw, const int *__restrict__ rl,
+                                             const float *__restrict__ res)
+{
+    const int n4 = 4 * nr;
+    int m = rl[k];
+    if (!(m & CHAIN_FIRST)) return;
+    const float *rs = res + (long long)s * nr * nt + n;
+    float a = rw[k] * rs[(long long)(k >> 2) * nt];
+    for (m &= CHAIN_FIRST - 1; m < n4; m = rl[m] & (CHAIN_FIRST - 1)) a += rw[m] * rs[(long long)(m >> 2) * nt];
+    const long long o = (long long)s * Np + ridx[k];
+    ap[o] += a;
+    accK[o] += a * pn1[o];
+}
+
+// Adds the residual R^T r_n into pbar^{n+1} and the receiver-cell term (R^T r_n) p^{n+1}
+// into the K accumulator; one thread per (shot, receiver footprint entry).
 __global__ void k_adj_inject_k(float *__restrict__ ap, float *__restrict__ accK, const float *__restrict__ pn1,
                                int ns, int nr, int nt, int n, long long Np, const long long *__restrict__ ridx,
-                               const float *__restrict__ rw, const float *__restrict__ res)
+                               const float *__restrict__ rw, const int *__restrict__ rl, const float *__restrict__ res)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ns * nr) return;
-    const int s = t / nr, r = t - s * nr;
-    const float v = res[(long long)t * nt + n];
-    const long long so = (long long)s * Np;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const long long o = so + ridx[4 * r + c];
-        const float a = rw[4 * r + c] * v;
-        atomicAdd(ap + o, a);
-        atomicAdd(accK + o, a * pn1[o]);
-    }
+    if (t >= ns * 4 * nr) return;
+    const int s = t / (4 * nr);
+    inject_entry(ap, accK, pn1, s, t - s * 4 * nr, nr, nt, n, Np, ridx, rw, rl, res);
 }
 
 // ------------------------------------------------------------------------ Born (S6)

@@ -22,6 +22,11 @@ experiments, Sec. "Almost Well-posed Example" and the scatterer table):
     receivers on a 1200 m circle; smooth random background (seeded normal fields, Gaussian
     filter sigma 50 cells, min-max scaled to vp 1500-3500 m/s and rho 1000-2500 kg/m^3) plus
     4 Gaussian anomalies (sigma 25 m, +-20 % in vp and rho, centres in a 600 m disc).
+  * ``batch_jobs`` -- uneven jobs for the batching and serving workloads: square grids with a
+    side drawn uniformly from 128 to 1024 nodes (dx 5 m, dt 0.5 ms, 8th order, 15 Hz), 500 to
+    4000 steps, 1 to 32 shots, n/4 receivers (32 to 256) on a circle of radius 0.4 (n - 1) dx,
+    a point or Gaussian scatterer (sigma 10 to 40 m) with seeded contrasts in [-0.3, 0.3].
+  * ``poisson_arrivals`` -- seeded Poisson request times.
   * ``small_case`` -- seeded random heterogeneous models on small grids for parity tests.
 """
 from __future__ import annotations
@@ -187,6 +192,36 @@ def config_smooth(nt=6000, ns=16, nr=256, n=1201, seed_vp=3, seed_rho=4, seed_an
                  circle(ns, 1200.0, c), circle(nr, 1200.0, c, 0.5), ricker(nt, 2.5e-4, 15.0),
                  sponge_v=4200.0)
     return w, ((vp_bg / 2000.0 - 1).astype(np.float32), (rho_bg / 2000.0 - 1).astype(np.float32))
+
+
+def batch_job(seed, side=(128, 1024), steps=(500, 4000), shots=(1, 32)):
+    """One uneven job of the batching/serving distribution (vp-rho contrasts of the true model)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(side[0], side[1] + 1))
+    nt = int(rng.integers(steps[0], steps[1] + 1))
+    ns = int(rng.integers(shots[0], shots[1] + 1))
+    nr = int(min(256, max(32, n // 4)))
+    dx, dt = 5.0, 5e-4
+    c = centre_of(n, n, dx)
+    if rng.random() < 0.5:
+        shape = point(n, n)
+    else:
+        shape = gaussian(n, n, dx, c, float(rng.uniform(10.0, 40.0)))
+    a, b = rng.uniform(-0.3, 0.3, size=2)
+    radius = 0.4 * (n - 1) * dx
+    return Workload(f"job-{n}x{n}-o8-t{nt}-s{ns}", n, n, dx, dt, nt, 8, 40, 2000.0, 2000.0, PZ_VP_RHO,
+                    (shape * np.float32(a)).astype(np.float32), (shape * np.float32(b)).astype(np.float32),
+                    circle(ns, radius, c, float(rng.random())), circle(nr, radius, c, 0.5), ricker(nt, dt, 15.0))
+
+
+def batch_jobs(count=256, seed=0, **kw):
+    """`count` jobs of batch_job's distribution, job k seeded (seed, k)."""
+    return [batch_job(np.random.SeedSequence([seed, k]), **kw) for k in range(count)]
+
+
+def poisson_arrivals(count, rate, seed=0):
+    """Arrival times (s) of a Poisson stream of `rate` requests per second."""
+    return np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=count))
 
 
 def small_case(seed=0, nx=45, nz=37, nt=120, order=8, sponge=6, ns=3, nr=7, pz=PZ_VP_RHO,
