@@ -16,6 +16,15 @@ forward steps are not counted) and FWI gradients per second.
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 launch with torch.distributed.run; every rank solves its own problems (different
 contrasts), so there is no collective on the data path ("weak" scaling).
+
+Two more workloads run through the batching engine (one JSON line each, 1 GPU):
+  --workload batch : 256 uneven jobs (square grids 128^2..1024^2, 500-4000 steps, 1-32 shots,
+                     point or Gaussian scatterers): their forward models (the observed data),
+                     then their misfit gradients at the background, each phase as one engine
+                     run; against the plain per-shot GPU path on a seeded sample of the jobs.
+  --workload serve : a seeded Poisson stream of mixed forward / Born / gradient requests with
+                     continuous batching; throughput and p50/p99 latency, against serving the
+                     same stream one request at a time through the single-job calls.
 """
 from __future__ import annotations
 
@@ -86,6 +95,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="gradient workspace budget (0: 80%% of free device memory)")
+    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "batch", "serve"])
+    ap.add_argument("--jobs", type=int, default=256, help="batch: number of jobs")
+    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--profile", action="store_true", help="batch/serve: per-kernel device time")
+    ap.add_argument("--sizes", default="light", choices=["light", "batch"],
+                    help="serve: request sizes (light: 128-256^2, 500-1000 steps, 1-4 shots; "
+                         "batch: the batch workload's distribution)")
     return ap.parse_args()
 
 
@@ -200,6 +217,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload != "gaussian":
+        from paper_1804_01184_gb300 import workloads
+        (workloads.bench_batch if args.workload == "batch" else workloads.bench_serve)(args, Clocks)
         return
     import numpy as np
     import torch

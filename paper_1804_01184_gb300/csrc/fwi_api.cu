@@ -135,7 +135,7 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
         P.st.nc[k] = -P.st.c[k];
     }
     P.ns = ns; P.nr = nr; P.nt = g->nt;
-    P.tz = g_tile_tz > 0 ? g_tile_tz : 64;
+    P.tz = g_tile_tz;   // 0: chosen per launch by strip_height()
     P.variant = g_tile_variant;
     P.B = std::max(1, std::min(B, std::max(ns, 1)));
     P.C = std::max(1, std::min(C, g->nt));
@@ -298,11 +298,57 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
     return FWI_OK;
 }
 
-// Warp-strip launch shape: one warp per (128-column strip, tz-row strip, shot), wpb warps a block.
-dim3 warp_grid(const Plan &P, int shots, int wpb = 2)
+// Warps of `kernel` (blocks of `threads`) resident on the whole GPU at once, from the
+// occupancy calculator; cached per kernel and device.
+int resident_warps(const void *kernel, int threads)
 {
-    const long long warps = (long long)((P.d.Nx + fwi::WS - 1) / fwi::WS) * ((P.d.Nz + P.tz - 1) / P.tz) * shots;
-    return dim3((unsigned)((warps + wpb - 1) / wpb));
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({kernel, dev});
+    if (it != cache.end()) return it->second;
+    int blocks = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        blocks = 1;
+        sms = 1;
+    }
+    const int w = std::max(1, blocks * (threads / 32) * sms);
+    cache[{kernel, dev}] = w;
+    return w;
+}
+
+// Strip height of a streaming launch (the tile-shape autotuner's rule).  A warp marches
+// down its strip row by row, so a launch lasts at least (tz + 4M - 1) row times, while the
+// row work of the whole launch grows as tz shrinks (each strip recomputes 4M - 1 halo rows).
+// Modelling the launch as max(one strip, total row work / resident warps), the best height
+// makes the strips just fill the resident warps: tz = column strips x rows x shots /
+// resident warps, rounded up to a multiple of 8 and kept within [8, 64].  fwi_set_tile's
+// height, when set, overrides the rule.  Any height gives bitwise identical results.
+long long strip_rows(const fwi::Dims &d, long long shots)
+{
+    return (long long)((d.Nx + fwi::WS - 1) / fwi::WS) * d.Nz * shots;
+}
+
+int strip_height_for_rows(long long rows, int resident)
+{
+    long long tz = (rows + resident - 1) / std::max(resident, 1);
+    tz = (tz + 7) / 8 * 8;
+    return (int)std::min<long long>(64, std::max<long long>(8, tz));
+}
+
+int strip_height(int fixed, const fwi::Dims &d, long long shots, int resident)
+{
+    return fixed > 0 ? fixed : strip_height_for_rows(strip_rows(d, shots), resident);
+}
+
+// Warp-strip launch shape: one warp per (120-column strip, tz-row strip, shot), wpb warps a block.
+dim3 warp_grid(const Plan &P, int tz, int shots, int wpb = 2)
+{
+    return dim3((unsigned)(((long long)fwi::strip_warps(P.d, tz, shots) + wpb - 1) / wpb));
 }
 
 fwi::Model model_of(const Plan &P, void *work)
@@ -325,8 +371,11 @@ struct Fwd {
         const fwi::Source src{at<long long>(work, P.sidx) + 4LL * s0, at<float>(work, P.sw) + 4LL * s0, wav};
         const float *vx0 = at<float>(work, P.vx[n & 1]), *vz0 = at<float>(work, P.vz[n & 1]);
         float *vx1 = at<float>(work, P.vx[(n + 1) & 1]), *vz1 = at<float>(work, P.vz[(n + 1) & 1]);
-        const dim3 grid = warp_grid(P, bg);
-        const fwi::FwdArgs args{p0, vx0, vz0, p1, vx1, vz1, model_of(P, work), d, P.st, src, n, P.tz, bg};
+        const int tz = strip_height(P.tz, d, bg,
+                                    resident_warps(P.M == 2 ? (const void *)fwi::k_fwd_warp<2, 1>
+                                                            : (const void *)fwi::k_fwd_warp<4, 1>, 64));
+        const dim3 grid = warp_grid(P, tz, bg);
+        const fwi::FwdArgs args{p0, vx0, vz0, p1, vx1, vz1, model_of(P, work), d, P.st, src, n, tz, bg};
         if (P.M == 2) {
             switch (P.variant) {
             case 1: LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, args); break;
@@ -433,8 +482,11 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
                        d.Np, at<long long>(work, P.ridx), at<float>(work, P.rw), at<int>(work, P.rl), res);
             const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
             float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
-            const dim3 grid = warp_grid(P, bg, 1);
-#define ADJ_ARGS fwi::AdjArgs{ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, P.tz, bg}
+            const int tz = strip_height(P.tz, d, bg,
+                                        resident_warps(P.M == 2 ? (const void *)fwi::k_adj_warp<2, 1>
+                                                                : (const void *)fwi::k_adj_warp<4, 1>, 32));
+            const dim3 grid = warp_grid(P, tz, bg, 1);
+#define ADJ_ARGS fwi::AdjArgs{ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, tz, bg}
             if (P.M == 2) {
                 switch (P.variant) {
                 case 1: LAUNCH((fwi::k_adj_warp<2, 8>), grid, 32, 0, st, ADJ_ARGS); break;
@@ -584,9 +636,12 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
             const int i = n & 1, o = (n + 1) & 1;
             auto F = [&](const size_t *a) { return at<float>(work, a[i]); };
             auto G = [&](const size_t *a) { return at<float>(work, a[o]); };
-            const dim3 grid = warp_grid(P, bg, 1);
+            const int tz = strip_height(P.tz, d, bg,
+                                        resident_warps(P.M == 2 ? (const void *)fwi::k_born_warp<2, 1>
+                                                                : (const void *)fwi::k_born_warp<4, 1>, 32));
+            const dim3 grid = warp_grid(P, tz, bg, 1);
 #define BORN_ARGS fwi::BornArgs{F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), \
-                  G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, P.tz, bg}
+                  G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, tz, bg}
             if (P.M == 2) {
                 if (P.variant == 2) LAUNCH((fwi::k_born_warp<2, 12>), grid, 32, 0, st, BORN_ARGS);
                 else LAUNCH((fwi::k_born_warp<2, 1>), grid, 32, 0, st, BORN_ARGS);

@@ -31,11 +31,7 @@ class Request:
     workload: object             # inputs.Workload (grid, model, acquisition, wavelet)
     dxi: tuple | None = None     # Born perturbation (host arrays)
     data: object = None          # gradient: observed traces (host array)
-    work_budget: int = 0
-
-    def cell_updates(self):
-        w = self.workload
-        return (w.nx + 2 * w.sponge) * (w.nz + 2 * w.sponge) * w.nt * w.ns
+    work_budget: int | None = None   # None: the serving loop's default budget
 
 
 def _pinned(a):
@@ -54,18 +50,24 @@ def stage(req: Request):
     return st
 
 
-def _submit(eng: E.Engine, req: Request, st):
+def _submit(eng: E.Engine, req: Request, st, budget):
     w = req.workload
     g = F.make_grid(**w.grid_kwargs())
     dev = lambda t: t.to("cuda", non_blocking=True)
     with torch.cuda.stream(eng.stream):
         a, b, src, wav, rec = dev(st["a"]), dev(st["b"]), dev(st["src"]), dev(st["wav"]), dev(st["rec"])
         if req.kind == E.JOB_MODEL:
-            return eng.submit_model(g, w.pz, a, b, src, wav, rec, work_budget=req.work_budget)
+            return eng.submit_model(g, w.pz, a, b, src, wav, rec, work_budget=budget)
         if req.kind == E.JOB_BORN:
-            return eng.submit_born(g, w.pz, a, b, dev(st["da"]), dev(st["db"]), src, wav, rec,
-                                   work_budget=req.work_budget)
-        return eng.submit_gradient(g, w.pz, a, b, src, wav, rec, dev(st["data"]), work_budget=req.work_budget)
+            return eng.submit_born(g, w.pz, a, b, dev(st["da"]), dev(st["db"]), src, wav, rec, work_budget=budget)
+        return eng.submit_gradient(g, w.pz, a, b, src, wav, rec, dev(st["data"]), work_budget=budget)
+
+
+def default_budget(arena_bytes):
+    """Workspace budget of a request: a 16th of the arena, so that all of a request's shots
+    run as one group when they fit (fewer, larger steps) while 16 large requests still
+    share the arena."""
+    return arena_bytes // 16
 
 
 def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=False):
@@ -73,6 +75,7 @@ def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=F
     Returns (stats, results) -- results[k] is the engine Result of request k when
     keep_results, else None."""
     eng = E.Engine(arena_bytes)
+    budget = default_budget(arena_bytes)
     staged = [stage(r) for r in requests]
     torch.cuda.synchronize()
     n = len(requests)
@@ -83,10 +86,12 @@ def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=F
     nxt = 0
     t0 = time.perf_counter()
     launches = 0
+    max_running = 0
     while nxt < n or ticket_of:
         now = time.perf_counter() - t0
         while nxt < n and arrivals[nxt] <= now:
-            ticket_of[_submit(eng, requests[nxt], staged[nxt])] = nxt
+            r = requests[nxt]
+            ticket_of[_submit(eng, r, staged[nxt], budget if r.work_budget is None else r.work_budget)] = nxt
             t_sub[nxt] = time.perf_counter() - t0
             nxt += 1
         if not ticket_of:                       # idle until the next arrival
@@ -98,11 +103,12 @@ def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=F
             if keep_results:
                 results[k] = res
         launches += F.launch_count()
+        max_running = max(max_running, eng.info()["running"])
     wall = time.perf_counter() - t0
     eng.close()
     lat = t_done - arrivals[:n]
-    cells = sum(r.cell_updates() for r in requests)
-    stats = dict(requests=n, wall_s=wall, req_per_s=n / wall, gcell_per_s=cells / wall / 1e9,
+    stats = dict(requests=n, wall_s=wall, req_per_s=n / wall,
                  p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
-                 mean_queue_ms=float(np.mean(t_sub - arrivals[:n]) * 1e3), launches=launches)
+                 mean_queue_ms=float(np.mean(t_sub - arrivals[:n]) * 1e3), launches=launches,
+                 max_running=max_running)
     return stats, results

@@ -1,0 +1,229 @@
+"""Batching and serving workloads measured through the engine (bench.py --workload batch|serve).
+
+Both print one JSON line.  Cell-updates count computational cells (sponge included) x steps
+x shots x propagation passes: forward modelling 1, Born 2 (background and scattered
+fields), gradient 2 (forward and adjoint; recomputed forward steps are not counted).
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import engine as E
+from . import fwi as F
+from . import inputs as I
+from . import serve as S
+
+METRIC = "Gcell-updates/s & FWI gradients/s vs plain per-shot GPU; p50/p99 solve latency"
+PASSES = {E.JOB_MODEL: 1, E.JOB_BORN: 2, E.JOB_GRADIENT: 2}
+OPS = {E.JOB_MODEL: F.OP_MODEL, E.JOB_BORN: F.OP_BORN, E.JOB_GRADIENT: F.OP_GRADIENT}
+
+
+def kernel_profile(enable):
+    """Per-kernel device time recorded by the library's launch events (fwi_profile)."""
+    import ctypes
+    L = F.lib()
+    if enable:
+        L.fwi_profile(1)
+        return None
+    buf = ctypes.create_string_buffer(1 << 16)
+    L.fwi_profile_report(buf, len(buf))
+    L.fwi_profile(0)
+    prof = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, tot = line.rsplit(" ", 2)
+        prof[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = (int(cnt), float(tot))
+    total = sum(v[1] for v in prof.values()) or 1.0
+    return {"device_ms": round(total, 1),
+            "kernels": {k: {"launches": c, "ms": round(t, 1), "share": round(t / total, 4)}
+                        for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+
+
+def cells(w):
+    return (w.nx + 2 * w.sponge) * (w.nz + 2 * w.sponge) * w.nt * w.ns
+
+
+def grid_of(w):
+    return F.make_grid(**w.grid_kwargs())
+
+
+def _drain(eng, ticket_jobs):
+    """Runs the engine until every ticket is done; returns (wall s, launches, results)."""
+    out, launches = {}, 0
+    t0 = time.perf_counter()
+    while len(out) < len(ticket_jobs):
+        for r in eng.run(32):
+            out[r.ticket] = r
+        launches += F.launch_count()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, launches, out
+
+
+def bench_batch(args, Clocks):
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    jobs = I.batch_jobs(args.jobs, seed=0)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    staged = [dict(a=d(w.xi_a), b=d(w.xi_b), src=d(w.src_xy), rec=d(w.rec_xy), wav=d(w.wavelet),
+                   zero=torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)) for w in jobs]
+    free, _ = torch.cuda.mem_get_info(dev)
+    # leave room for every job's traces and float64 gradients
+    outputs = sum(w.ns * w.nr * w.nt * 4 + 80 * w.nx * w.nz + 8 for w in jobs)
+    arena = int((free - outputs) * 0.85) // 256 * 256
+    eng = E.Engine(arena)
+    grad_budget = arena // 16
+    total_fwd = sum(cells(w) for w in jobs)
+
+    clocks = Clocks(0)
+    clocks.start()
+    if args.profile:
+        kernel_profile(True)
+    # phase A: observed data of the true models (all shots of a job in one group when it fits)
+    tickets = [eng.submit_model(grid_of(w), w.pz, s["a"], s["b"], s["src"], s["wav"], s["rec"],
+                                work_budget=min(grad_budget, 1 << 62)) for w, s in zip(jobs, staged)]
+    t_model, l_model, res = _drain(eng, tickets)
+    data = [res[t].traces for t in tickets]
+    # phase B: misfit and gradient of every job at the background model
+    tickets = [eng.submit_gradient(grid_of(w), w.pz, s["zero"], s["zero"], s["src"], s["wav"], s["rec"], dd,
+                                   work_budget=grad_budget) for w, s, dd in zip(jobs, staged, data)]
+    t_grad, l_grad, res = _drain(eng, tickets)
+    clk = clocks.stop()
+    prof = kernel_profile(False) if args.profile else None
+    finite = all(bool(torch.isfinite(res[t].grads).all()) for t in tickets[:8])
+    eng.close()
+
+    value = (total_fwd + 2 * total_fwd) / (t_model + t_grad) / 1e9
+    plain = plain_per_shot_batch(jobs, staged, data, dev)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": round(1e3 * (t_model + t_grad), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch-{args.jobs}-uneven", "jobs": args.jobs,
+                   "sizes": "square 128^2..1024^2 (+40-cell sponge), 500-4000 steps, 1-32 shots, 8th order",
+                   "arena_gb": round(arena / 2**30, 1), "gradient_budget_gb": round(grad_budget / 2**30, 2),
+                   "l2": "working set larger than L2"},
+        "forward": {"value": round(total_fwd / t_model / 1e9, 3), "seconds": round(t_model, 2),
+                    "launches": l_model},
+        "gradient": {"value": round(2 * total_fwd / t_grad / 1e9, 3), "seconds": round(t_grad, 2),
+                     "gradients_per_s": round(args.jobs / t_grad, 3), "launches": l_grad, "finite": finite},
+        "plain_per_shot": plain,
+        "speedup_vs_plain": round(value / plain["value"], 2) if plain["value"] else None,
+        "gpu_launches": l_model + l_grad, "clocks": clk,
+    }
+    if prof:
+        out["profile"] = prof
+    print(json.dumps(out), flush=True)
+
+
+def plain_per_shot_batch(jobs, staged, data, dev, sample=16):
+    """The plain per-shot GPU path on a seeded sample of the jobs: for the first `sample` jobs,
+    shot 0 alone through fwi_model and fwi_gradient (one call each, workspace for one shot)."""
+    upd, t = 0, 0.0
+    for w, s, dd in list(zip(jobs, staged, data))[:sample]:
+        g = grid_of(w)
+        src = s["src"][:1]
+        wm = F.workspace(g, 1, w.nr, F.OP_MODEL, 1 << 62)
+        wg = F.workspace(g, 1, w.nr, F.OP_GRADIENT, 1 << 36)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F.fwi_model(g, w.pz, s["a"], s["b"], src, s["wav"], s["rec"], work=wm, check=False)
+        F.fwi_gradient(g, w.pz, s["zero"], s["zero"], src, s["wav"], s["rec"], dd[:1], work=wg, check=False)
+        torch.cuda.synchronize()
+        t += time.perf_counter() - t0
+        upd += 3 * cells(w) // w.ns
+        del wm, wg
+    return {"value": round(upd / t / 1e9, 3), "unit": "Gcell-updates/s",
+            "sample": f"shot 0 of the first {sample} jobs, model + gradient, one call each"}
+
+
+# ------------------------------------------------------------------------------ serving
+
+LIGHT = dict(side=(128, 256), steps=(500, 1000), shots=(1, 4))
+
+
+def serve_requests(count, seed, **job_kw):
+    """`count` requests, kinds uniform over forward / Born / gradient, sizes from
+    inputs.batch_job(**job_kw)."""
+    rng = np.random.default_rng(seed)
+    kw = job_kw
+    reqs = []
+    for k in range(count):
+        w = I.batch_job(np.random.SeedSequence([seed, 7, k]), **kw)
+        kind = int(rng.integers(0, 3))
+        r = S.Request(kind, w)
+        if kind == E.JOB_BORN:
+            r.dxi = (w.xi_a * np.float32(0.5), w.xi_b * np.float32(0.5))
+            w.xi_a, w.xi_b = w.background()
+        if kind == E.JOB_GRADIENT:
+            r.data = I.random_like((w.ns, w.nr, w.nt), 10_000 + k, 1e3)
+        reqs.append(r)
+    return reqs
+
+
+def serve_plain(requests, arrivals):
+    """The same stream served one request at a time through the single-job calls."""
+    n = len(requests)
+    staged = [S.stage(r) for r in requests]
+    done = np.zeros(n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, r in enumerate(requests):
+        now = time.perf_counter() - t0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        w, st = r.workload, staged[k]
+        g = grid_of(w)
+        dv = lambda t: t.to("cuda", non_blocking=True)
+        a, b, src, wav, rec = dv(st["a"]), dv(st["b"]), dv(st["src"]), dv(st["wav"]), dv(st["rec"])
+        if r.kind == E.JOB_MODEL:
+            F.fwi_model(g, w.pz, a, b, src, wav, rec, check=False)
+        elif r.kind == E.JOB_BORN:
+            F.fwi_born(g, w.pz, a, b, dv(st["da"]), dv(st["db"]), src, wav, rec, check=False)
+        else:
+            F.fwi_gradient(g, w.pz, a, b, src, wav, rec, dv(st["data"]), check=False)
+        torch.cuda.synchronize()
+        done[k] = time.perf_counter() - t0
+    lat = done - arrivals[:n]
+    upd = sum(PASSES[r.kind] * cells(r.workload) for r in requests)
+    return {"req_per_s": round(n / done[-1], 2), "gcell_per_s": round(upd / done[-1] / 1e9, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+            "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2)}
+
+
+def bench_serve(args, Clocks):
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    reqs = serve_requests(args.requests, seed=1, **(LIGHT if args.sizes == "light" else {}))
+    arrivals = I.poisson_arrivals(len(reqs), args.rate, seed=2)
+    free, _ = torch.cuda.mem_get_info(dev)
+    arena = int(free * 0.6) // 256 * 256
+    # the engine: warm-up on the first few requests, then the timed stream
+    S.serve(reqs[:4], np.zeros(4), arena)
+    clocks = Clocks(0)
+    clocks.start()
+    if args.profile:
+        kernel_profile(True)
+    stats, _ = S.serve(reqs, arrivals, arena)
+    prof = kernel_profile(False) if args.profile else None
+    clk = clocks.stop()
+    plain = serve_plain(reqs, arrivals) if args.sizes == "light" else None
+    upd = sum(PASSES[r.kind] * cells(r.workload) for r in reqs)
+    out = {
+        "metric": METRIC, "value": round(upd / stats["wall_s"] / 1e9, 3), "unit": "Gcell-updates/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * stats["wall_s"], 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serve-{args.sizes}-poisson{args.rate:g}", "requests": len(reqs),
+                   "rate_per_s": args.rate, "mix": "forward / Born / gradient, uniform",
+                   "sizes": ("square 128^2..256^2, 500-1000 steps, 1-4 shots" if args.sizes == "light" else
+                             "square 128^2..1024^2, 500-4000 steps, 1-32 shots"),
+                   "arena_gb": round(arena / 2**30, 1)},
+        "serving": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()},
+        "plain_one_at_a_time": plain,
+        "gpu_launches": stats["launches"], "clocks": clk,
+    }
+    if prof:
+        out["profile"] = prof
+    print(json.dumps(out), flush=True)

@@ -283,3 +283,27 @@ def test_adjoint_with_receivers_sharing_cells_is_deterministic(F):
     for pz in range(5):
         for k in range(2):
             assert rel_l2(G[pz, k], ref[pz, k]) <= GRAD_TOL
+
+
+def test_strip_heights_give_bitwise_identical_results(F):
+    """The strip height only partitions the grid among warps: every height (fixed, or chosen
+    per launch) gives bitwise identical traces, Born traces and gradients."""
+    w = I.small_case(seed=23, nx=70, nz=83, nt=120, order=8, sponge=6, ns=3, nr=5)
+    g = gpu_grid(w)
+    da, db = I.random_like(w.xi_a.shape, 3, 0.05), I.random_like(w.xi_a.shape, 4, 0.05)
+    data = I.random_like((w.ns, w.nr, w.nt), 5, 1e3)
+    out = []
+    try:
+        for tz in (0, 8, 16, 24, 64, 200):
+            F.fwi_set_tile(tz, 0)
+            tr = run_model(F, w)
+            bo = F.fwi_born(g, w.pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy).cpu().numpy()
+            J, G = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, data)
+            out.append((tr, bo, J.item(), G.cpu().numpy()))
+    finally:
+        F.fwi_set_tile(0, 0)
+    for o in out[1:]:
+        np.testing.assert_array_equal(o[0], out[0][0])
+        np.testing.assert_array_equal(o[1], out[0][1])
+        assert o[2] == out[0][2]
+        np.testing.assert_array_equal(o[3], out[0][3])
