@@ -12,6 +12,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -298,10 +299,30 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
     return FWI_OK;
 }
 
-// Warps of `kernel` (blocks of `threads`) resident on the whole GPU at once, from the
-// occupancy calculator; cached per kernel and device.
-int resident_warps(const void *kernel, int threads)
+// Opts `kernel` in to `bytes` of dynamic shared memory (once per kernel and device).
+void dyn_smem(const void *kernel, size_t bytes)
 {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.insert({kernel, dev}).second) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Launch of a streaming kernel with `smem` bytes of dynamic shared memory.
+#define SLAUNCH(kernel, grid, block, smem, stream, ...)            \
+    do {                                                           \
+        dyn_smem((const void *)kernel, smem);                      \
+        LAUNCH(kernel, grid, block, smem, stream, __VA_ARGS__);    \
+    } while (0)
+
+// Warps of `kernel` (blocks of `threads`, `smem` bytes of dynamic shared memory) resident on
+// the whole GPU at once, from the occupancy calculator; cached per kernel and device.
+int resident_warps(const void *kernel, int threads, size_t smem)
+{
+    dyn_smem(kernel, smem);
     static std::mutex mu;
     static std::map<std::pair<const void *, int>, int> cache;
     int dev = 0;
@@ -310,7 +331,7 @@ int resident_warps(const void *kernel, int threads)
     auto it = cache.find({kernel, dev});
     if (it != cache.end()) return it->second;
     int blocks = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         blocks = 1;
@@ -371,22 +392,25 @@ struct Fwd {
         const fwi::Source src{at<long long>(work, P.sidx) + 4LL * s0, at<float>(work, P.sw) + 4LL * s0, wav};
         const float *vx0 = at<float>(work, P.vx[n & 1]), *vz0 = at<float>(work, P.vz[n & 1]);
         float *vx1 = at<float>(work, P.vx[(n + 1) & 1]), *vz1 = at<float>(work, P.vz[(n + 1) & 1]);
+        constexpr int T = 32 * fwi::FWD_WPB;
+        const size_t S = P.M == 2 ? fwi::fwd_smem<2>() : fwi::fwd_smem<4>();
         const int tz = strip_height(P.tz, d, bg,
                                     resident_warps(P.M == 2 ? (const void *)fwi::k_fwd_warp<2, 1>
-                                                            : (const void *)fwi::k_fwd_warp<4, 1>, 64));
-        const dim3 grid = warp_grid(P, tz, bg);
+                                                            : (const void *)fwi::k_fwd_warp<4, 1>, T, S));
+        const dim3 grid = warp_grid(P, tz, bg, fwi::FWD_WPB);
         const fwi::FwdArgs args{p0, vx0, vz0, p1, vx1, vz1, model_of(P, work), d, P.st, src, n, tz, bg};
+        constexpr int B128 = fwi::minb(128, T), B170 = fwi::minb(170, T);
         if (P.M == 2) {
             switch (P.variant) {
-            case 1: LAUNCH((fwi::k_fwd_warp<2, 8>), grid, 64, 0, st, args); break;
-            case 2: LAUNCH((fwi::k_fwd_warp<2, 6>), grid, 64, 0, st, args); break;
-            default: LAUNCH((fwi::k_fwd_warp<2, 1>), grid, 64, 0, st, args);
+            case 1: SLAUNCH((fwi::k_fwd_warp<2, B128>), grid, T, S, st, args); break;
+            case 2: SLAUNCH((fwi::k_fwd_warp<2, B170>), grid, T, S, st, args); break;
+            default: SLAUNCH((fwi::k_fwd_warp<2, 1>), grid, T, S, st, args);
             }
         } else {
             switch (P.variant) {
-            case 1: LAUNCH((fwi::k_fwd_warp<4, 8>), grid, 64, 0, st, args); break;
-            case 2: LAUNCH((fwi::k_fwd_warp<4, 6>), grid, 64, 0, st, args); break;
-            default: LAUNCH((fwi::k_fwd_warp<4, 1>), grid, 64, 0, st, args);
+            case 1: SLAUNCH((fwi::k_fwd_warp<4, B128>), grid, T, S, st, args); break;
+            case 2: SLAUNCH((fwi::k_fwd_warp<4, B170>), grid, T, S, st, args); break;
+            default: SLAUNCH((fwi::k_fwd_warp<4, 1>), grid, T, S, st, args);
             }
         }
     }
@@ -482,22 +506,24 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
                        d.Np, at<long long>(work, P.ridx), at<float>(work, P.rw), at<int>(work, P.rl), res);
             const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
             float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
+            const size_t S = P.M == 2 ? fwi::adj_smem<2>() : fwi::adj_smem<4>();
             const int tz = strip_height(P.tz, d, bg,
                                         resident_warps(P.M == 2 ? (const void *)fwi::k_adj_warp<2, 1>
-                                                                : (const void *)fwi::k_adj_warp<4, 1>, 32));
+                                                                : (const void *)fwi::k_adj_warp<4, 1>, 32, S));
             const dim3 grid = warp_grid(P, tz, bg, 1);
 #define ADJ_ARGS fwi::AdjArgs{ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, tz, bg}
+            constexpr int B128 = fwi::minb(128, 32), B170 = fwi::minb(170, 32);
             if (P.M == 2) {
                 switch (P.variant) {
-                case 1: LAUNCH((fwi::k_adj_warp<2, 8>), grid, 32, 0, st, ADJ_ARGS); break;
-                case 2: LAUNCH((fwi::k_adj_warp<2, 6>), grid, 32, 0, st, ADJ_ARGS); break;
-                default: LAUNCH((fwi::k_adj_warp<2, 1>), grid, 32, 0, st, ADJ_ARGS);
+                case 1: SLAUNCH((fwi::k_adj_warp<2, B128>), grid, 32, S, st, ADJ_ARGS); break;
+                case 2: SLAUNCH((fwi::k_adj_warp<2, B170>), grid, 32, S, st, ADJ_ARGS); break;
+                default: SLAUNCH((fwi::k_adj_warp<2, 1>), grid, 32, S, st, ADJ_ARGS);
                 }
             } else {
                 switch (P.variant) {
-                case 1: LAUNCH((fwi::k_adj_warp<4, 8>), grid, 32, 0, st, ADJ_ARGS); break;
-                case 2: LAUNCH((fwi::k_adj_warp<4, 6>), grid, 32, 0, st, ADJ_ARGS); break;
-                default: LAUNCH((fwi::k_adj_warp<4, 1>), grid, 32, 0, st, ADJ_ARGS);
+                case 1: SLAUNCH((fwi::k_adj_warp<4, B128>), grid, 32, S, st, ADJ_ARGS); break;
+                case 2: SLAUNCH((fwi::k_adj_warp<4, B170>), grid, 32, S, st, ADJ_ARGS); break;
+                default: SLAUNCH((fwi::k_adj_warp<4, 1>), grid, 32, S, st, ADJ_ARGS);
                 }
             }
 #undef ADJ_ARGS
@@ -636,18 +662,20 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
             const int i = n & 1, o = (n + 1) & 1;
             auto F = [&](const size_t *a) { return at<float>(work, a[i]); };
             auto G = [&](const size_t *a) { return at<float>(work, a[o]); };
+            const size_t S = P.M == 2 ? fwi::born_smem<2>() : fwi::born_smem<4>();
             const int tz = strip_height(P.tz, d, bg,
                                         resident_warps(P.M == 2 ? (const void *)fwi::k_born_warp<2, 1>
-                                                                : (const void *)fwi::k_born_warp<4, 1>, 32));
+                                                                : (const void *)fwi::k_born_warp<4, 1>, 32, S));
             const dim3 grid = warp_grid(P, tz, bg, 1);
 #define BORN_ARGS fwi::BornArgs{F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), \
                   G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, tz, bg}
+            constexpr int B170 = fwi::minb(170, 32);
             if (P.M == 2) {
-                if (P.variant == 2) LAUNCH((fwi::k_born_warp<2, 12>), grid, 32, 0, st, BORN_ARGS);
-                else LAUNCH((fwi::k_born_warp<2, 1>), grid, 32, 0, st, BORN_ARGS);
+                if (P.variant == 2) SLAUNCH((fwi::k_born_warp<2, B170>), grid, 32, S, st, BORN_ARGS);
+                else SLAUNCH((fwi::k_born_warp<2, 1>), grid, 32, S, st, BORN_ARGS);
             } else {
-                if (P.variant == 2) LAUNCH((fwi::k_born_warp<4, 12>), grid, 32, 0, st, BORN_ARGS);
-                else LAUNCH((fwi::k_born_warp<4, 1>), grid, 32, 0, st, BORN_ARGS);
+                if (P.variant == 2) SLAUNCH((fwi::k_born_warp<4, B170>), grid, 32, S, st, BORN_ARGS);
+                else SLAUNCH((fwi::k_born_warp<4, 1>), grid, 32, S, st, BORN_ARGS);
             }
 #undef BORN_ARGS
             if (P.nr > 0)

@@ -6,7 +6,7 @@
 //     float4 left of the strip (x0-4) and lane 31 the one right of it (x0+120), each with one
 //     more pressure float4 (x0-8, x0+124).  They compute the v_x halo values the divergence of
 //     the strip's edge columns needs, so no lane ever runs a divergent halo branch.
-//   - z-neighbours: shared rings of p-like rows (WRP deep) and a register queue of v_z rows.
+//   - z-neighbours: shared rings of p-like rows (2M + WPD deep) and a register queue of v_z rows.
 //   - x-neighbours: a shared row (columns x0-8 .. x0+135) per field.
 //   - Global rows arrive by 16-byte cp.async (zero-filled outside the grid) WPD rows ahead.
 //   - Element-wise updates and z-stencils use packed FP32x2 arithmetic.
@@ -22,9 +22,26 @@ constexpr int WS = 120;    // columns owned by a warp
 constexpr int WH = 8;      // shared offset of column x0
 constexpr int WROW = 144;  // shared row: columns x0-8 .. x0+135
 constexpr int WPD = 2;     // rows prefetched ahead
-constexpr int WRP = 16;    // depth of the p-like rings (power of two, >= 2M + WPD)
-constexpr int WNS = 4;     // depth of the staged rows (power of two, >= WPD + 1)
-static_assert(WRP >= 2 * 4 + WPD && WNS >= WPD + 1, "ring too shallow");
+constexpr int FWD_WPB = 2; // warps per block of the forward kernels
+
+// Slot of row g + c in a ring of N rows, for the row g the loop is at (|c| < N); the ring
+// position of g advances by one per row, so no division is needed.
+template <int N>
+struct RingPos {
+    int b = 0;   // g mod N
+    __device__ __forceinline__ int operator()(int c) const
+    {
+        int s = b + c;
+        if (c < 0) s += s < 0 ? N : 0;
+        if (c > 0) s -= s >= N ? N : 0;
+        return s;
+    }
+    __device__ __forceinline__ void next() { b = b + 1 == N ? 0 : b + 1; }
+};
+
+// The streaming kernels keep their per-warp staging in dynamic shared memory (deep stagings
+// exceed the 48 KB static limit); fwd_smem<M>(), adj_smem<M>() and born_smem<M>() give the bytes
+// per block.
 
 struct Strip {
     int x0, z0, s;      // strip origin and shot
@@ -109,6 +126,13 @@ __device__ __forceinline__ void cp16(void *dst, const float *base, int off, bool
                  "r"(valid ? 16 : 0)
                  : "memory");
 }
+// 4-byte asynchronous copy of base[off] (zero when !valid), as cp16
+__device__ __forceinline__ void cp4(void *dst, const float *base, int off, bool valid)
+{
+    const float *src = base + (valid ? off : 0);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -145,17 +169,20 @@ struct FwdArgs {
     int n, tz, nshots;
 };
 
-// Shared memory of one warp of a forward launch.
+// Shared memory of one warp of a forward launch (2M + WPD pressure rows: the 2M the stencils
+// read and the WPD in flight; WPD + 1 stages).
+template <int M>
 struct FwdSmem {
-    float ring[WRP][WROW];          // p^n rows
-    float stg[WNS][5][WROW];        // vz, bz (row f-M); vx, bx, K (row j)
+    float ring[2 * M + WPD][WROW];  // p^n rows
+    float stg[WPD + 1][5][WROW];    // vz, bz (row f-M); vx, bx, K (row j)
     float vxr[2][WROW];             // v_x^{n+1/2} rows
+    float scl[WPD + 1][4];          // az(j), azh(r) of each stage
 };
 
 template <int M>
-__device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdSmem &sh)
+__device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdSmem<M> &sh)
 {
-    constexpr int R = 2 * M;
+    constexpr int R = 2 * M, NP = 2 * M + WPD, NS = WPD + 1;
     const Dims &d = a.d;
     const Model &mo = a.mo;
     const Stencil &st = a.st;
@@ -174,11 +201,12 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
     const bool hsrc = strip_has_src(sc, sp.x0, z0, zend);
-    auto issue = [&](int g) {
+    // stage row g (rows f = f0 + g; r = f - M; j = f - 2M + 1) into ring slot ps, stage ss
+    auto issue = [&](int g, int ps, int ss) {
         const int f = f0 + g, r = f - M, j = f - R + 1;
         const bool vf = f >= 0 && f < d.Nz, vr = r >= 0 && r < d.Nz, vj = j >= 0 && j < d.Nz;
-        float *pr = ring[g & (WRP - 1)];
-        float(*sg)[WROW] = stg[g & (WNS - 1)];
+        float *pr = ring[ps];
+        float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
         cp16(pr + L.mo, P0, of + L.mc, vf && L.in);
         if (!L.own) cp16(pr + L.eo, P0, of + L.ec, vf && L.ein);
@@ -187,30 +215,35 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         cp16(sg[2] + L.mo, VX0, oj + L.mc, vj && L.in);
         cp16(sg[3] + L.mo, mo.bx, oj + L.mc, vj && L.in);
         cp16(sg[4] + L.mo, mo.K, oj + L.mc, vj && L.in && L.own);
+        if (lane == 0) {
+            cp4(&sh.scl[ss][0], mo.az, j, vj);
+            cp4(&sh.scl[ss][1], mo.azh, r, vr);
+        }
         cp_commit();
     };
     float4 vq[R];   // vz rows r-2M+1 .. r (oldest first), shifted every row
 #pragma unroll
     for (int k = 0; k < R; ++k) vq[k] = f4(0.f);
 #pragma unroll
-    for (int g = 0; g < WPD; ++g) issue(g);
+    for (int g = 0; g < WPD; ++g) issue(g, g, g);
+    RingPos<NP> P;      // ring position of row g
+    RingPos<NS> S;      // stage of row g
     const int fend = zend + R - 1;
 #pragma unroll 1
     for (int f = f0; f < fend; ++f) {
         const int g = f - f0;
         __syncwarp();                 // every lane is done with the slots issue() refills
-        issue(g + WPD);
+        issue(g + WPD, P(WPD), S(WPD));
         cp_wait<WPD>();               // stage g has landed (for this lane) ...
         __syncwarp();                 // ... and for every lane
-        float(*sg)[WROW] = stg[g & (WNS - 1)];
-        // vz at half node r + 1/2, r = f - M: p rows r-M+1 .. r+M = stages g-2M+1 .. g
+        float(*sg)[WROW] = stg[S(0)];
+        const float az = sh.scl[S(0)][0], azh = sh.scl[S(0)][1];
+        // vz at half node r + 1/2, r = f - M: p rows r-M+1 .. r+M = rows g-2M+1 .. g
         const int r = f - M;
         float4 gz = f4(0.f);          // -dt D+z p
 #pragma unroll
         for (int k = 1; k <= M; ++k)
-            gz = ptap(st.nc[k - 1], ld4(ring[(g - M + k) & (WRP - 1)] + L.mo),
-                      ld4(ring[(g - M - k + 1) & (WRP - 1)] + L.mo), gz);
-        const float azh = (r >= 0 && r < d.Nz) ? __ldg(mo.azh + r) : 0.f;
+            gz = ptap(st.nc[k - 1], ld4(ring[P(k - M)] + L.mo), ld4(ring[P(1 - M - k)] + L.mo), gz);
         const float4 vz = pmul(pmul(azh, axv), pfma(ld4(sg[1] + L.mo), gz, ld4(sg[0] + L.mo)));
         if (L.wr && r >= z0 && r < zend) st4(VZ1 + r * d.Px + L.mc, vz);
 #pragma unroll
@@ -219,8 +252,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         // v_x at row j = f - 2M + 1 (every lane: own columns and the two halo float4)
         const int j = f - R + 1;
         const bool row = j >= z0 && j < zend;
-        const float az = (j >= 0 && j < d.Nz) ? __ldg(mo.az + j) : 0.f;
-        const float *prow = ring[(g - R + 1) & (WRP - 1)];
+        const float *prow = ring[P(1 - R)];
         const float4 gx = row_dplus<M>(prow, L.mo, st.nc);        // -dt D+x p
         const float4 vx = pmul(pmul(az, axhv), pfma(ld4(sg[3] + L.mo), gx, ld4(sg[2] + L.mo)));
         float *vrow = vxr[f & 1];
@@ -242,33 +274,39 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
             }
             st4(P1 + j * d.Px + L.mc, pn);
         }
+        P.next();
+        S.next();
     }
     cp_wait<0>();
 }
 
+// MINB: blocks per SM the register budget is sized for (1: unbounded); minb() gives the
+// MINB that caps a block of `threads` threads at `regs` registers a thread
+constexpr int minb(int regs, int threads) { return 65536 / (regs * threads); }
+
 template <int M, int MINB>
-__global__ void __launch_bounds__(64, MINB) k_fwd_warp(FwdArgs a)
+__global__ void __launch_bounds__(32 * FWD_WPB, MINB) k_fwd_warp(FwdArgs a)
 {
-    __shared__ __align__(16) FwdSmem sh[2];
+    extern __shared__ __align__(16) unsigned char fwi_smem[];
     bool valid;
-    const Strip sp = strip_of(a.d, a.tz, a.nshots, 2, valid);
+    const Strip sp = strip_of(a.d, a.tz, a.nshots, FWD_WPB, valid);
     if (!valid) return;
-    fwd_body<M>(a, sp, sh[(threadIdx.x >> 5) & 1]);
+    fwd_body<M>(a, sp, reinterpret_cast<FwdSmem<M> *>(fwi_smem)[threadIdx.x >> 5]);
 }
 
 // One time step of several independent jobs: warp w runs strip (w - wstart[j]) of job j.
 template <int M>
-__global__ void __launch_bounds__(64) k_fwd_batch(const __grid_constant__ BatchTable<FwdArgs> t)
+__global__ void __launch_bounds__(32 * FWD_WPB) k_fwd_batch(const __grid_constant__ BatchTable<FwdArgs> t)
 {
-    __shared__ __align__(16) FwdSmem sh[2];
-    const int w = blockIdx.x * 2 + (threadIdx.x >> 5);
+    extern __shared__ __align__(16) unsigned char fwi_smem[];
+    const int w = blockIdx.x * FWD_WPB + (threadIdx.x >> 5);
     if (w >= t.wstart[t.njobs]) return;
     int local;
     const FwdArgs &a = t.jobs[job_of(w, t.wstart, t.njobs, local)];
     bool valid;
     const Strip sp = strip_at(local, a.d, a.tz, a.nshots, valid);
     if (!valid) return;
-    fwd_body<M>(a, sp, sh[(threadIdx.x >> 5) & 1]);
+    fwd_body<M>(a, sp, reinterpret_cast<FwdSmem<M> *>(fwi_smem)[threadIdx.x >> 5]);
 }
 
 // ------------------------------------------------------------- adjoint step (S7)
@@ -292,17 +330,19 @@ struct AdjArgs {
 };
 
 // Shared memory of one adjoint warp.
+template <int M>
 struct AdjSmem {
-    float pr[WRP][WROW];              // p^n rows
-    float qr[8][WROW];                // K d_p pbar^{n+1} rows (2M <= 8)
-    float stg[WNS][7][WROW];          // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
+    float pr[2 * M + WPD][WROW];      // p^n rows
+    float qr[2 * M][WROW];            // K d_p pbar^{n+1} rows
+    float stg[WPD + 1][7][WROW];      // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
     float bur[2][WROW];               // bx u_x rows
+    float scl[WPD + 1][4];            // az(f), azh(r), az(j) of each stage
 };
 
 template <int M>
-__device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjSmem &sh)
+__device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjSmem<M> &sh)
 {
-    constexpr int R = 2 * M, NF = 7;
+    constexpr int R = 2 * M, NF = 7, NP = 2 * M + WPD, NS = WPD + 1;
     const Dims &d = a.d;
     const Model &mo = a.mo;
     const Stencil &st = a.st;
@@ -322,12 +362,17 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const float4 axe = ldg_if(mo.ax + L.ec, L.ein);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
-    auto issue = [&](int g) {
+    auto issue = [&](int g, int ps, int ss) {
         const int f = f0 + g, r = f - M, j = f - R + 1;
         const bool vf = f >= 0 && f < d.Nz, vr = r >= 0 && r < d.Nz, vj = j >= 0 && j < d.Nz;
-        float *prow = pr[g & (WRP - 1)];
-        float(*sg)[WROW] = stg[g & (WNS - 1)];
+        float *prow = pr[ps];
+        float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
+        if (lane == 0) {
+            cp4(&sh.scl[ss][0], mo.az, f, vf);
+            cp4(&sh.scl[ss][1], mo.azh, r, vr);
+            cp4(&sh.scl[ss][2], mo.az, j, vj);
+        }
         cp16(prow + L.mo, PN, of + L.mc, vf && L.in);
         cp16(sg[0] + L.mo, A0, of + L.mc, vf && L.in);
         cp16(sg[1] + L.mo, mo.K, of + L.mc, vf && L.in);
@@ -349,23 +394,26 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
 #pragma unroll
     for (int k = 0; k < R; ++k) { qq[k] = f4(0.f); bq[k] = f4(0.f); }
 #pragma unroll
-    for (int g = 0; g < WPD; ++g) issue(g);
+    for (int g = 0; g < WPD; ++g) issue(g, g, g);
+    RingPos<NP> P;      // ring position of row g in pr
+    RingPos<NS> S;      // stage of row g
+    RingPos<R> Q;       // ring position of row g in qr
     const int fend = zend + R - 1;
 #pragma unroll 1
     for (int f = f0; f < fend; ++f) {
         const int g = f - f0;
         __syncwarp();
-        issue(g + WPD);
+        issue(g + WPD, P(WPD), S(WPD));
         cp_wait<WPD>();
         __syncwarp();
-        float(*sg)[WROW] = stg[g & (WNS - 1)];
+        float(*sg)[WROW] = stg[S(0)];
+        const float azf = sh.scl[S(0)][0], azh = sh.scl[S(0)][1], az = sh.scl[S(0)][2];
         // q row f = K d_p pbar^{n+1} (main float4; halo lanes also the extra float4)
-        const float azf = (f >= 0 && f < d.Nz) ? __ldg(mo.az + f) : 0.f;
         const float4 qf = pmul(pmul(azf, axv), pmul(ld4(sg[1] + L.mo), ld4(sg[0] + L.mo)));
 #pragma unroll
         for (int q = 0; q < R - 1; ++q) qq[q] = qq[q + 1];
         qq[R - 1] = qf;
-        float *qrow = qr[g & (R - 1)];
+        float *qrow = qr[Q(0)];
         st4(qrow + L.mo, qf);
         if (!L.own) st4(qrow + L.eo, pmul(pmul(azf, axe), pmul(ld4(sg[1] + L.eo), ld4(sg[0] + L.eo))));
         // u_z at half node r + 1/2, r = f - M
@@ -374,9 +422,8 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
 #pragma unroll
         for (int k = 1; k <= M; ++k) {   // qq[q] is row f - 2M + 1 + q = r - M + 1 + q
             gq = ptap(st.c[k - 1], qq[M - 1 + k], qq[M - k], gq);
-            gp = ptap(st.c[k - 1], ld4(pr[(g - M + k) & (WRP - 1)] + L.mo), ld4(pr[(g - M - k + 1) & (WRP - 1)] + L.mo), gp);
+            gp = ptap(st.c[k - 1], ld4(pr[P(k - M)] + L.mo), ld4(pr[P(1 - M - k)] + L.mo), gp);
         }
-        const float azh = (r >= 0 && r < d.Nz) ? __ldg(mo.azh + r) : 0.f;
         const float4 uz = pmul(pmul(azh, axv), padd(ld4(sg[2] + L.mo), gq));
 #pragma unroll
         for (int q = 0; q < R - 1; ++q) bq[q] = bq[q + 1];
@@ -388,14 +435,13 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
         // u_x at row j = f - 2M + 1 (every lane: own columns and the two halo float4)
         const int j = f - R + 1;
         const bool row = j >= z0 && j < zend;
-        const float az = (j >= 0 && j < d.Nz) ? __ldg(mo.az + j) : 0.f;
-        const int sj = (g - R + 1) & (R - 1), pj = (g - R + 1) & (WRP - 1);
-        const float4 ux = pmul(pmul(az, axhv), padd(ld4(sg[4] + L.mo), row_dplus<M>(qr[sj], L.mo, st.c)));
+        const float *pj = pr[P(1 - R)];
+        const float4 ux = pmul(pmul(az, axhv), padd(ld4(sg[4] + L.mo), row_dplus<M>(qr[Q(1 - R)], L.mo, st.c)));
         float *brow = bur[f & 1];
         st4(brow + L.mo, pmul(ld4(sg[5] + L.mo), ux));
         if (row && L.wr) {
             st4(AX1 + j * d.Px + L.mc, ux);
-            red_add4(GX + j * d.Px + L.mc, pmul(ux, row_dplus<M>(pr[pj], L.mo, st.c)));
+            red_add4(GX + j * d.Px + L.mc, pmul(ux, row_dplus<M>(pj, L.mo, st.c)));
         }
         __syncwarp();
         if (row && L.wr) {
@@ -406,26 +452,30 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
             const float4 dp = pmul(az, axv);
             st4(A1 + j * d.Px + L.mc, pfma(dp, ld4(sg[6] + L.mo), dv));
             // pbar^n - d_p pbar^{n+1} is exactly the divergence term dv
-            red_add4(GK + j * d.Px + L.mc, pmul(ld4(pr[pj] + L.mo), dv));
+            red_add4(GK + j * d.Px + L.mc, pmul(ld4(pj + L.mo), dv));
         }
+        P.next();
+        S.next();
+        Q.next();
     }
     cp_wait<0>();
 }
 
 template <int M, int MINB>
-__global__ void __launch_bounds__(32, 2 * MINB) k_adj_warp(AdjArgs a)
+__global__ void __launch_bounds__(32, MINB) k_adj_warp(AdjArgs a)
 {
-    __shared__ __align__(16) AdjSmem sh;   // one warp per block
+    extern __shared__ __align__(16) unsigned char fwi_smem[];   // one warp per block
     bool valid;
     const Strip sp = strip_of(a.d, a.tz, a.nshots, 1, valid);
     if (!valid) return;
-    adj_body<M>(a, sp, sh);
+    adj_body<M>(a, sp, *reinterpret_cast<AdjSmem<M> *>(fwi_smem));
 }
 
 template <int M>
 __global__ void __launch_bounds__(32) k_adj_batch(const __grid_constant__ BatchTable<AdjArgs> t)
 {
-    __shared__ __align__(16) AdjSmem sh;
+    extern __shared__ __align__(16) unsigned char fwi_smem[];
+    AdjSmem<M> &sh = *reinterpret_cast<AdjSmem<M> *>(fwi_smem);
     const int w = blockIdx.x;
     if (w >= t.wstart[t.njobs]) return;
     int local;
@@ -486,18 +536,20 @@ struct BornArgs {
     int n, tz, nshots;
 };
 
+template <int M>
 struct BornSmem {
-    float pr[WRP][WROW];
-    float qr[WRP][WROW];
+    float pr[2 * M + WPD][WROW];
+    float qr[2 * M + WPD][WROW];
     float stg[WPD + 1][10][WROW];
     float vr[2][WROW];
     float ur[2][WROW];
+    float scl[WPD + 1][4];            // az(j), azh(r) of each stage
 };
 
 template <int M>
-__device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, BornSmem &sh)
+__device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, BornSmem<M> &sh)
 {
-    constexpr int R = 2 * M, NS = WPD + 1, NF = 10;
+    constexpr int R = 2 * M, NS = WPD + 1, NF = 10, NP = 2 * M + WPD;
     const Dims &d = a.d;
     const Model &mo = a.mo;
     const Pert &pe = a.pe;
@@ -521,12 +573,16 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
     const bool hsrc = strip_has_src(sc, sp.x0, z0, zend);
-    auto issue = [&](int g) {
+    auto issue = [&](int g, int ps, int ss) {
         const int f = f0 + g, r = f - M, j = f - R + 1;
         const bool vf = f >= 0 && f < d.Nz, vr = r >= 0 && r < d.Nz, vj = j >= 0 && j < d.Nz;
-        float *pr = spr[g & (WRP - 1)], *qr = sqr[g & (WRP - 1)];
-        float(*sg)[WROW] = stg[g % NS];
+        float *pr = spr[ps], *qr = sqr[ps];
+        float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
+        if (lane == 0) {
+            cp4(&sh.scl[ss][0], mo.az, j, vj);
+            cp4(&sh.scl[ss][1], mo.azh, r, vr);
+        }
         const bool zo = vr && L.in && L.own, xo = vj && L.in;
         cp16(pr + L.mo, P0, of + L.mc, vf && L.in);
         cp16(qr + L.mo, Q0, of + L.mc, vf && L.in);
@@ -550,25 +606,27 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
 #pragma unroll
     for (int k = 0; k < R; ++k) { vq[k] = f4(0.f); uq[k] = f4(0.f); }
 #pragma unroll
-    for (int g = 0; g < WPD; ++g) issue(g);
+    for (int g = 0; g < WPD; ++g) issue(g, g, g);
+    RingPos<NP> P;      // ring position of row g
+    RingPos<NS> S;      // stage of row g
     const int fend = zend + R - 1;
 #pragma unroll 1
     for (int f = f0; f < fend; ++f) {
         const int g = f - f0;
         __syncwarp();
-        issue(g + WPD);
+        issue(g + WPD, P(WPD), S(WPD));
         cp_wait<WPD>();
         __syncwarp();
-        float(*sg)[WROW] = stg[g % NS];
+        float(*sg)[WROW] = stg[S(0)];
+        const float az = sh.scl[S(0)][0], azh = sh.scl[S(0)][1];
         const int r = f - M;
         float4 gp = f4(0.f), gq = f4(0.f);     // -dt D+z p, -dt D+z q
 #pragma unroll
         for (int k = 1; k <= M; ++k) {
-            const int a = (g - M + k) & (WRP - 1), b = (g - M - k + 1) & (WRP - 1);
+            const int a = P(k - M), b = P(1 - M - k);
             gp = ptap(st.nc[k - 1], ld4(spr[a] + L.mo), ld4(spr[b] + L.mo), gp);
             gq = ptap(st.nc[k - 1], ld4(sqr[a] + L.mo), ld4(sqr[b] + L.mo), gq);
         }
-        const float azh = (r >= 0 && r < d.Nz) ? __ldg(mo.azh + r) : 0.f;
         const float4 fz = pmul(azh, axv), bz = ld4(sg[2] + L.mo);
         const float4 vz = pmul(fz, pfma(bz, gp, ld4(sg[0] + L.mo)));
         const float4 uz = pmul(fz, pfma(ld4(sg[3] + L.mo), gp, pfma(bz, gq, ld4(sg[1] + L.mo))));
@@ -582,8 +640,7 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         uq[R - 1] = uz;
         const int j = f - R + 1;
         const bool row = j >= z0 && j < zend;
-        const float az = (j >= 0 && j < d.Nz) ? __ldg(mo.az + j) : 0.f;
-        const int sj = (g - R + 1) & (WRP - 1);
+        const int sj = P(1 - R);
         const float *prow = spr[sj], *qrow = sqr[sj];
         const float4 fx = pmul(az, axhv), bx = ld4(sg[6] + L.mo);
         const float4 gpx = row_dplus<M>(prow, L.mo, st.nc);
@@ -619,6 +676,8 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
             st4(P1 + j * d.Px + L.mc, pn);
             st4(Q1 + j * d.Px + L.mc, qn);
         }
+        P.next();
+        S.next();
     }
     cp_wait<0>();
 }
@@ -626,17 +685,18 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
 template <int M, int MINB>
 __global__ void __launch_bounds__(32, MINB) k_born_warp(BornArgs a)
 {
-    __shared__ __align__(16) BornSmem sh;
+    extern __shared__ __align__(16) unsigned char fwi_smem[];
     bool valid;
     const Strip sp = strip_of(a.d, a.tz, a.nshots, 1, valid);
     if (!valid) return;
-    born_body<M>(a, sp, sh);
+    born_body<M>(a, sp, *reinterpret_cast<BornSmem<M> *>(fwi_smem));
 }
 
 template <int M>
 __global__ void __launch_bounds__(32) k_born_batch(const __grid_constant__ BatchTable<BornArgs> t)
 {
-    __shared__ __align__(16) BornSmem sh;
+    extern __shared__ __align__(16) unsigned char fwi_smem[];
+    BornSmem<M> &sh = *reinterpret_cast<BornSmem<M> *>(fwi_smem);
     const int w = blockIdx.x;
     if (w >= t.wstart[t.njobs]) return;
     int local;
@@ -646,6 +706,16 @@ __global__ void __launch_bounds__(32) k_born_batch(const __grid_constant__ Batch
     if (!valid) return;
     born_body<M>(a, sp, sh);
 }
+
+// dynamic shared memory of one block of each family
+template <int M>
+constexpr size_t fwd_smem() { return sizeof(FwdSmem<M>) * FWD_WPB; }
+template <int M>
+constexpr size_t adj_smem() { return sizeof(AdjSmem<M>); }
+template <int M>
+constexpr size_t born_smem() { return sizeof(BornSmem<M>); }
+static_assert(fwd_smem<4>() <= 227 * 1024 && adj_smem<4>() <= 227 * 1024 && born_smem<4>() <= 227 * 1024,
+              "staging exceeds the shared memory of a block");
 
 static_assert(sizeof(BatchTable<FwdArgs>) <= 32000 && sizeof(BatchTable<AdjArgs>) <= 32000 &&
                   sizeof(BatchTable<BornArgs>) <= 32000,
