@@ -6,9 +6,11 @@
 //     float4 left of the strip (x0-4) and lane 31 the one right of it (x0+120), each with one
 //     more pressure float4 (x0-8, x0+124).  They compute the v_x halo values the divergence of
 //     the strip's edge columns needs, so no lane ever runs a divergent halo branch.
-//   - z-neighbours: shared rings of p-like rows (2M + WPD deep) and a register queue of v_z rows.
+//   - z-neighbours: shared rings of p-like rows (2M + the prefetch depth) and a register queue
+//     of v_z rows.
 //   - x-neighbours: a shared row (columns x0-8 .. x0+135) per field.
-//   - Global rows arrive by 16-byte cp.async (zero-filled outside the grid) WPD rows ahead.
+//   - Global rows arrive by 16-byte cp.async (zero-filled outside the grid) FWD_WPD, ADJ_WPD
+//     or BORN_WPD rows ahead.
 //   - Element-wise updates and z-stencils use packed FP32x2 arithmetic.
 // Every value outside the computational grid is zero: the model and sponge arrays are zero in
 // the padding columns, so every update there is exactly zero; every own lane whose float4
@@ -21,7 +23,11 @@ namespace fwi {
 constexpr int WS = 120;    // columns owned by a warp
 constexpr int WH = 8;      // shared offset of column x0
 constexpr int WROW = 144;  // shared row: columns x0-8 .. x0+135
-constexpr int WPD = 2;     // rows prefetched ahead
+// rows each family prefetches ahead (measured on GB300: deeper staging costs shared memory,
+// hence resident warps; these depths balance the two)
+constexpr int FWD_WPD = 3;
+constexpr int ADJ_WPD = 3;
+constexpr int BORN_WPD = 2;
 constexpr int FWD_WPB = 2; // warps per block of the forward kernels
 
 // Slot of row g + c in a ring of N rows, for the row g the loop is at (|c| < N); the ring
@@ -169,20 +175,20 @@ struct FwdArgs {
     int n, tz, nshots;
 };
 
-// Shared memory of one warp of a forward launch (2M + WPD pressure rows: the 2M the stencils
-// read and the WPD in flight; WPD + 1 stages).
+// Shared memory of one warp of a forward launch (2M + FWD_WPD pressure rows: the 2M the stencils
+// read and the FWD_WPD in flight; FWD_WPD + 1 stages).
 template <int M>
 struct FwdSmem {
-    float ring[2 * M + WPD][WROW];  // p^n rows
-    float stg[WPD + 1][5][WROW];    // vz, bz (row f-M); vx, bx, K (row j)
+    float ring[2 * M + FWD_WPD][WROW];  // p^n rows
+    float stg[FWD_WPD + 1][5][WROW];    // vz, bz (row f-M); vx, bx, K (row j)
     float vxr[2][WROW];             // v_x^{n+1/2} rows
-    float scl[WPD + 1][4];          // az(j), azh(r) of each stage
+    float scl[FWD_WPD + 1][4];          // az(j), azh(r) of each stage
 };
 
 template <int M>
 __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdSmem<M> &sh)
 {
-    constexpr int R = 2 * M, NP = 2 * M + WPD, NS = WPD + 1;
+    constexpr int R = 2 * M, NP = 2 * M + FWD_WPD, NS = FWD_WPD + 1;
     const Dims &d = a.d;
     const Model &mo = a.mo;
     const Stencil &st = a.st;
@@ -225,16 +231,16 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
 #pragma unroll
     for (int k = 0; k < R; ++k) vq[k] = f4(0.f);
 #pragma unroll
-    for (int g = 0; g < WPD; ++g) issue(g, g, g);
+    for (int g = 0; g < FWD_WPD; ++g) issue(g, g, g);
     RingPos<NP> P;      // ring position of row g
     RingPos<NS> S;      // stage of row g
     const int fend = zend + R - 1;
-#pragma unroll 1
+#pragma unroll 2   // two rows per trip: half the register-queue shifts (measured: 1 < 2 > 4)
     for (int f = f0; f < fend; ++f) {
         const int g = f - f0;
         __syncwarp();                 // every lane is done with the slots issue() refills
-        issue(g + WPD, P(WPD), S(WPD));
-        cp_wait<WPD>();               // stage g has landed (for this lane) ...
+        issue(g + FWD_WPD, P(FWD_WPD), S(FWD_WPD));
+        cp_wait<FWD_WPD>();               // stage g has landed (for this lane) ...
         __syncwarp();                 // ... and for every lane
         float(*sg)[WROW] = stg[S(0)];
         const float az = sh.scl[S(0)][0], azh = sh.scl[S(0)][1];
@@ -332,17 +338,17 @@ struct AdjArgs {
 // Shared memory of one adjoint warp.
 template <int M>
 struct AdjSmem {
-    float pr[2 * M + WPD][WROW];      // p^n rows
+    float pr[2 * M + ADJ_WPD][WROW];      // p^n rows
     float qr[2 * M][WROW];            // K d_p pbar^{n+1} rows
-    float stg[WPD + 1][7][WROW];      // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
+    float stg[ADJ_WPD + 1][7][WROW];      // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
     float bur[2][WROW];               // bx u_x rows
-    float scl[WPD + 1][4];            // az(f), azh(r), az(j) of each stage
+    float scl[ADJ_WPD + 1][4];            // az(f), azh(r), az(j) of each stage
 };
 
 template <int M>
 __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjSmem<M> &sh)
 {
-    constexpr int R = 2 * M, NF = 7, NP = 2 * M + WPD, NS = WPD + 1;
+    constexpr int R = 2 * M, NF = 7, NP = 2 * M + ADJ_WPD, NS = ADJ_WPD + 1;
     const Dims &d = a.d;
     const Model &mo = a.mo;
     const Stencil &st = a.st;
@@ -394,17 +400,17 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
 #pragma unroll
     for (int k = 0; k < R; ++k) { qq[k] = f4(0.f); bq[k] = f4(0.f); }
 #pragma unroll
-    for (int g = 0; g < WPD; ++g) issue(g, g, g);
+    for (int g = 0; g < ADJ_WPD; ++g) issue(g, g, g);
     RingPos<NP> P;      // ring position of row g in pr
     RingPos<NS> S;      // stage of row g
     RingPos<R> Q;       // ring position of row g in qr
     const int fend = zend + R - 1;
-#pragma unroll 1
+#pragma unroll 2   // two rows per trip: half the register-queue shifts (measured: 1 < 2 > 4)
     for (int f = f0; f < fend; ++f) {
         const int g = f - f0;
         __syncwarp();
-        issue(g + WPD, P(WPD), S(WPD));
-        cp_wait<WPD>();
+        issue(g + ADJ_WPD, P(ADJ_WPD), S(ADJ_WPD));
+        cp_wait<ADJ_WPD>();
         __syncwarp();
         float(*sg)[WROW] = stg[S(0)];
         const float azf = sh.scl[S(0)][0], azh = sh.scl[S(0)][1], az = sh.scl[S(0)][2];
@@ -538,18 +544,18 @@ struct BornArgs {
 
 template <int M>
 struct BornSmem {
-    float pr[2 * M + WPD][WROW];
-    float qr[2 * M + WPD][WROW];
-    float stg[WPD + 1][10][WROW];
+    float pr[2 * M + BORN_WPD][WROW];
+    float qr[2 * M + BORN_WPD][WROW];
+    float stg[BORN_WPD + 1][10][WROW];
     float vr[2][WROW];
     float ur[2][WROW];
-    float scl[WPD + 1][4];            // az(j), azh(r) of each stage
+    float scl[BORN_WPD + 1][4];            // az(j), azh(r) of each stage
 };
 
 template <int M>
 __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, BornSmem<M> &sh)
 {
-    constexpr int R = 2 * M, NS = WPD + 1, NF = 10, NP = 2 * M + WPD;
+    constexpr int R = 2 * M, NS = BORN_WPD + 1, NF = 10, NP = 2 * M + BORN_WPD;
     const Dims &d = a.d;
     const Model &mo = a.mo;
     const Pert &pe = a.pe;
@@ -606,16 +612,16 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
 #pragma unroll
     for (int k = 0; k < R; ++k) { vq[k] = f4(0.f); uq[k] = f4(0.f); }
 #pragma unroll
-    for (int g = 0; g < WPD; ++g) issue(g, g, g);
+    for (int g = 0; g < BORN_WPD; ++g) issue(g, g, g);
     RingPos<NP> P;      // ring position of row g
     RingPos<NS> S;      // stage of row g
     const int fend = zend + R - 1;
-#pragma unroll 1
+#pragma unroll 2   // two rows per trip: half the register-queue shifts (measured: 1 < 2 > 4)
     for (int f = f0; f < fend; ++f) {
         const int g = f - f0;
         __syncwarp();
-        issue(g + WPD, P(WPD), S(WPD));
-        cp_wait<WPD>();
+        issue(g + BORN_WPD, P(BORN_WPD), S(BORN_WPD));
+        cp_wait<BORN_WPD>();
         __syncwarp();
         float(*sg)[WROW] = stg[S(0)];
         const float az = sh.scl[S(0)][0], azh = sh.scl[S(0)][1];
