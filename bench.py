@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--profile", action="store_true", help="batch/serve: per-kernel device time")
+    ap.add_argument("--capacity-run", type=int, default=0,
+                    help="serve: requests of a second stream at 80%% of the first stream's throughput")
     ap.add_argument("--sizes", default="light", choices=["light", "batch"],
                     help="serve: request sizes (light: 128-256^2, 500-1000 steps, 1-4 shots; "
                          "batch: the batch workload's distribution)")

@@ -23,9 +23,10 @@ experiments, Sec. "Almost Well-posed Example" and the scatterer table):
     filter sigma 50 cells, min-max scaled to vp 1500-3500 m/s and rho 1000-2500 kg/m^3) plus
     4 Gaussian anomalies (sigma 25 m, +-20 % in vp and rho, centres in a 600 m disc).
   * ``batch_jobs`` -- uneven jobs for the batching and serving workloads: square grids with a
-    side drawn uniformly from 128 to 1024 nodes (dx 5 m, dt 0.5 ms, 8th order, 15 Hz), 500 to
-    4000 steps, 1 to 32 shots, n/4 receivers (32 to 256) on a circle of radius 0.4 (n - 1) dx,
-    a point or Gaussian scatterer (sigma 10 to 40 m) with seeded contrasts in [-0.3, 0.3].
+    side drawn uniformly from 128 to 1024 nodes (+ 40-cell sponge; dx 5 m, dt 0.5 ms, 8th
+    order, 15 Hz), 500 to 4000 steps, 1 to 32 shots, 64 receivers, sources and receivers on a
+    circle of radius 0.35 n dx, a point or Gaussian scatterer (sigma 10 to 40 m, each with
+    probability 1/2) with contrasts drawn uniformly from [-0.5, 0.5] in vp and in rho.
   * ``poisson_arrivals`` -- seeded Poisson request times.
   * ``small_case`` -- seeded random heterogeneous models on small grids for parity tests.
 """
@@ -200,15 +201,15 @@ def batch_job(seed, side=(128, 1024), steps=(500, 4000), shots=(1, 32)):
     n = int(rng.integers(side[0], side[1] + 1))
     nt = int(rng.integers(steps[0], steps[1] + 1))
     ns = int(rng.integers(shots[0], shots[1] + 1))
-    nr = int(min(256, max(32, n // 4)))
+    nr = 64
     dx, dt = 5.0, 5e-4
     c = centre_of(n, n, dx)
     if rng.random() < 0.5:
         shape = point(n, n)
     else:
         shape = gaussian(n, n, dx, c, float(rng.uniform(10.0, 40.0)))
-    a, b = rng.uniform(-0.3, 0.3, size=2)
-    radius = 0.4 * (n - 1) * dx
+    a, b = rng.uniform(-0.5, 0.5, size=2)
+    radius = 0.35 * n * dx
     return Workload(f"job-{n}x{n}-o8-t{nt}-s{ns}", n, n, dx, dt, nt, 8, 40, 2000.0, 2000.0, PZ_VP_RHO,
                     (shape * np.float32(a)).astype(np.float32), (shape * np.float32(b)).astype(np.float32),
                     circle(ns, radius, c, float(rng.random())), circle(nr, radius, c, 0.5), ricker(nt, dt, 15.0))

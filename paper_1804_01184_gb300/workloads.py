@@ -196,7 +196,8 @@ def serve_plain(requests, arrivals):
 def bench_serve(args, Clocks):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    reqs = serve_requests(args.requests, seed=1, **(LIGHT if args.sizes == "light" else {}))
+    kw = LIGHT if args.sizes == "light" else {}
+    reqs = serve_requests(args.requests, seed=1, **kw)
     arrivals = I.poisson_arrivals(len(reqs), args.rate, seed=2)
     free, _ = torch.cuda.mem_get_info(dev)
     arena = int(free * 0.6) // 256 * 256
@@ -224,6 +225,14 @@ def bench_serve(args, Clocks):
         "plain_one_at_a_time": plain,
         "gpu_launches": stats["launches"], "clocks": clk,
     }
+    if args.capacity_run > 0:
+        # a second stream at 80 % of the throughput the first one reached
+        rate = 0.8 * stats["req_per_s"]
+        reqs2 = serve_requests(args.capacity_run, seed=3, **kw)
+        arr2 = I.poisson_arrivals(len(reqs2), rate, seed=4)
+        st2, _ = S.serve(reqs2, arr2, arena)
+        out["at_80pct_capacity"] = {"rate_per_s": round(rate, 3),
+                                    **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in st2.items()}}
     if prof:
         out["profile"] = prof
     print(json.dumps(out), flush=True)
