@@ -171,12 +171,14 @@ int fwi_model_noalloc(const fwi_grid *g, fwi_param pz, const float *xi_a, const 
 int fwi_set_checkpoint(int every);
 
 /* Launch-shape tuning (no counterpart in the paper: the tile-shape autotuner's hook).  By
- * default the strip height of the streaming kernels is chosen for every launch from the
- * launch's size and the kernel's occupancy, so that the strips just fill the warps the GPU
- * holds at once (between 8 and 64 rows).  tz > 0 (a multiple of 8) fixes it instead, for
- * plans made afterwards by any thread (0 restores the automatic choice); variant picks the
- * register budget per thread of the single-job kernels (0 = unbounded, 1 = 128, 2 = 170).
- * Results are bitwise identical for every setting; only speed changes. */
+ * default the strip height of the streaming kernels is tuned online: for each launch shape
+ * the first launches try the height an occupancy rule picks (strips that just fill the warps
+ * the GPU holds at once) and a few others, each timed twice with CUDA events on the
+ * launching stream without blocking, and the shape then keeps its fastest height (launches
+ * under stream capture are not timed).  tz > 0 (a multiple of 8) fixes the height instead,
+ * for plans made afterwards by any thread (0 restores tuning); variant picks the register
+ * budget per thread of the single-job kernels (0 = unbounded, 1 = 128, 2 = 170).  Results are
+ * bitwise identical for every setting; only speed changes. */
 int fwi_set_tile(int tz, int variant);
 
 /* ---------------------------------------------------------------------------------------

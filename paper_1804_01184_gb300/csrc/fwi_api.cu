@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <set>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -361,9 +362,168 @@ int strip_height_for_rows(long long rows, int resident)
     return (int)std::min<long long>(64, std::max<long long>(8, tz));
 }
 
+// Online strip-height tuner (the measured half of the autotuner).  For each launch shape --
+// (kernel, grid, shots) for the single-job calls, (kernel, quarter-octave bucket of the total
+// strip rows) for the engine's batched launches -- the first launches try candidate heights
+// (the rule's height and 32 .. 120), each twice, timed by an event pair on the launching
+// stream.  The timings are collected without blocking as later launches of the same shape
+// arrive; once every candidate has two, the shape keeps its fastest height.  Launches under
+// stream capture are not timed and use the rule's height (or the shape's chosen one).
+class StripTuner {
+public:
+    struct Slot {
+        int tz = 0;
+        size_t cand = 0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool timed = false;
+    };
+    using Key = std::tuple<const void *, long long, long long, int>;
+
+    // Height for the next launch of shape `key` on `st`; when the launch is to be timed the
+    // start event is already recorded and finish(slot) must follow the launch.
+    Slot pick(const Key &key, int rule, cudaStream_t st)
+    {
+        Slot s;
+        s.tz = rule;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return s;
+        }
+        std::lock_guard<std::mutex> lk(mu_);
+        Shape &sh = shapes_[key];
+        if (sh.cand.empty()) init(sh, rule);
+        poll(sh);
+        if (sh.chosen) {
+            s.tz = sh.chosen;
+            return s;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return s;
+        size_t best = sh.cand.size();
+        for (size_t k = 0; k < sh.cand.size(); ++k) {
+            const size_t c = (sh.next + k) % sh.cand.size();
+            if (sh.nsamp[c] + sh.inflight[c] < SAMPLES) { best = c; break; }
+        }
+        if (best == sh.cand.size()) return s;     // every sample is in flight
+        sh.next = best + 1;
+        s.tz = sh.cand[best];
+        s.cand = best;
+        s.e0 = event();
+        s.e1 = event();
+        if (!s.e0 || !s.e1 || cudaEventRecord(s.e0, st) != cudaSuccess) {
+            cudaGetLastError();
+            release(s);
+            s.tz = rule;
+            return s;
+        }
+        s.timed = true;
+        ++sh.inflight[best];
+        return s;
+    }
+
+    void finish(const Key &key, Slot &s, cudaStream_t st)
+    {
+        if (!s.timed) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        Shape &sh = shapes_[key];
+        if (cudaEventRecord(s.e1, st) != cudaSuccess) {
+            cudaGetLastError();
+            --sh.inflight[s.cand];
+            release(s);
+            return;
+        }
+        sh.pending.push_back(s);
+    }
+
+private:
+    static constexpr int SAMPLES = 2;
+    struct Shape {
+        std::vector<int> cand, nsamp, inflight;
+        std::vector<float> best;
+        std::deque<Slot> pending;
+        size_t next = 0;
+        int chosen = 0;
+    };
+
+    void init(Shape &sh, int rule)
+    {
+        std::set<int> c = {rule, 32, 40, 48, 56, 64, 80, 96, 120};
+        sh.cand.assign(c.begin(), c.end());
+        sh.nsamp.assign(sh.cand.size(), 0);
+        sh.inflight.assign(sh.cand.size(), 0);
+        sh.best.assign(sh.cand.size(), 1e30f);
+    }
+
+    void poll(Shape &sh)
+    {
+        while (!sh.pending.empty()) {
+            Slot &s = sh.pending.front();
+            const cudaError_t q = cudaEventQuery(s.e1);
+            if (q == cudaErrorNotReady) break;
+            float ms = 0.f;
+            if (q == cudaSuccess && cudaEventElapsedTime(&ms, s.e0, s.e1) == cudaSuccess) {
+                sh.best[s.cand] = std::min(sh.best[s.cand], ms);
+                ++sh.nsamp[s.cand];
+            } else {
+                cudaGetLastError();
+            }
+            --sh.inflight[s.cand];
+            release(s);
+            sh.pending.pop_front();
+        }
+        if (sh.chosen) return;
+        for (size_t c = 0; c < sh.cand.size(); ++c)
+            if (sh.nsamp[c] < SAMPLES) return;
+        size_t b = 0;
+        for (size_t c = 1; c < sh.cand.size(); ++c)
+            if (sh.best[c] < sh.best[b]) b = c;
+        sh.chosen = sh.cand[b];
+    }
+
+    cudaEvent_t event()
+    {
+        if (!pool_.empty()) {
+            cudaEvent_t e = pool_.back();
+            pool_.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+
+    void release(Slot &s)
+    {
+        if (s.e0) pool_.push_back(s.e0);
+        if (s.e1) pool_.push_back(s.e1);
+        s.e0 = s.e1 = nullptr;
+    }
+
+    std::mutex mu_;
+    std::map<Key, Shape> shapes_;
+    std::vector<cudaEvent_t> pool_;
+};
+
+StripTuner g_tuner;
+
 int strip_height(int fixed, const fwi::Dims &d, long long shots, int resident)
 {
     return fixed > 0 ? fixed : strip_height_for_rows(strip_rows(d, shots), resident);
+}
+
+// Strip height of a single-job launch: fixed, or tuned per (kernel, grid, shots).  Returns the
+// tuner slot the caller closes with g_tuner.finish() after the launch.
+StripTuner::Slot tuned_height(int fixed, const void *kernel, const fwi::Dims &d, int shots, int resident,
+                              cudaStream_t st, StripTuner::Key &key)
+{
+    StripTuner::Slot s;
+    s.tz = strip_height(fixed, d, shots, resident);
+    if (fixed > 0) return s;
+    key = StripTuner::Key{kernel, ((long long)d.Nx << 32) | (unsigned)d.Nz, shots, 0};
+    return g_tuner.pick(key, s.tz, st);
 }
 
 // Warp-strip launch shape: one warp per (120-column strip, tz-row strip, shot), wpb warps a block.
@@ -394,9 +554,10 @@ struct Fwd {
         float *vx1 = at<float>(work, P.vx[(n + 1) & 1]), *vz1 = at<float>(work, P.vz[(n + 1) & 1]);
         constexpr int T = 32 * fwi::FWD_WPB;
         const size_t S = P.M == 2 ? fwi::fwd_smem<2>() : fwi::fwd_smem<4>();
-        const int tz = strip_height(P.tz, d, bg,
-                                    resident_warps(P.M == 2 ? (const void *)fwi::k_fwd_warp<2, 1>
-                                                            : (const void *)fwi::k_fwd_warp<4, 1>, T, S));
+        const void *K0 = P.M == 2 ? (const void *)fwi::k_fwd_warp<2, 1> : (const void *)fwi::k_fwd_warp<4, 1>;
+        StripTuner::Key key;
+        StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, T, S), st, key);
+        const int tz = ts.tz;
         const dim3 grid = warp_grid(P, tz, bg, fwi::FWD_WPB);
         const fwi::FwdArgs args{p0, vx0, vz0, p1, vx1, vz1, model_of(P, work), d, P.st, src, n, tz, bg};
         constexpr int B128 = fwi::minb(128, T), B170 = fwi::minb(170, T);
@@ -413,6 +574,7 @@ struct Fwd {
             default: SLAUNCH((fwi::k_fwd_warp<4, 1>), grid, T, S, st, args);
             }
         }
+        g_tuner.finish(key, ts, st);
     }
 
     void sample(int n, int bg, int nr, const float *p, float *traces) const
@@ -507,9 +669,10 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
             const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
             float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
             const size_t S = P.M == 2 ? fwi::adj_smem<2>() : fwi::adj_smem<4>();
-            const int tz = strip_height(P.tz, d, bg,
-                                        resident_warps(P.M == 2 ? (const void *)fwi::k_adj_warp<2, 1>
-                                                                : (const void *)fwi::k_adj_warp<4, 1>, 32, S));
+            const void *K0 = P.M == 2 ? (const void *)fwi::k_adj_warp<2, 1> : (const void *)fwi::k_adj_warp<4, 1>;
+            StripTuner::Key key;
+            StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, 32, S), st, key);
+            const int tz = ts.tz;
             const dim3 grid = warp_grid(P, tz, bg, 1);
 #define ADJ_ARGS fwi::AdjArgs{ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, tz, bg}
             constexpr int B128 = fwi::minb(128, 32), B170 = fwi::minb(170, 32);
@@ -526,6 +689,7 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
                 default: SLAUNCH((fwi::k_adj_warp<4, 1>), grid, 32, S, st, ADJ_ARGS);
                 }
             }
+            g_tuner.finish(key, ts, st);
 #undef ADJ_ARGS
         }
     }
@@ -663,9 +827,10 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
             auto F = [&](const size_t *a) { return at<float>(work, a[i]); };
             auto G = [&](const size_t *a) { return at<float>(work, a[o]); };
             const size_t S = P.M == 2 ? fwi::born_smem<2>() : fwi::born_smem<4>();
-            const int tz = strip_height(P.tz, d, bg,
-                                        resident_warps(P.M == 2 ? (const void *)fwi::k_born_warp<2, 1>
-                                                                : (const void *)fwi::k_born_warp<4, 1>, 32, S));
+            const void *K0 = P.M == 2 ? (const void *)fwi::k_born_warp<2, 1> : (const void *)fwi::k_born_warp<4, 1>;
+            StripTuner::Key key;
+            StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, 32, S), st, key);
+            const int tz = ts.tz;
             const dim3 grid = warp_grid(P, tz, bg, 1);
 #define BORN_ARGS fwi::BornArgs{F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), \
                   G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, tz, bg}
@@ -677,6 +842,7 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
                 if (P.variant == 2) SLAUNCH((fwi::k_born_warp<4, B170>), grid, 32, S, st, BORN_ARGS);
                 else SLAUNCH((fwi::k_born_warp<4, 1>), grid, 32, S, st, BORN_ARGS);
             }
+            g_tuner.finish(key, ts, st);
 #undef BORN_ARGS
             if (P.nr > 0)
                 LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, G(P.dp), bg, P.nr, P.nt, n, d.Np,
