@@ -310,6 +310,8 @@ void dyn_smem(const void *kernel, size_t bytes)
     std::lock_guard<std::mutex> lk(mu);
     if (!done.insert({kernel, dev}).second) return;
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // the whole unified L1/shared array as shared memory: the staging, not L1, holds the reuse
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 // Launch of a streaming kernel with `smem` bytes of dynamic shared memory.

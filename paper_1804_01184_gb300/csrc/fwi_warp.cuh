@@ -8,7 +8,7 @@
 //     the strip's edge columns needs, so no lane ever runs a divergent halo branch.
 //   - z-neighbours: shared rings of p-like rows (2M + the prefetch depth) and a register queue
 //     of v_z rows.
-//   - x-neighbours: a shared row (columns x0-8 .. x0+135) per field.
+//   - x-neighbours: a shared row (columns x0-8 .. x0+127) per field.
 //   - Global rows arrive by 16-byte cp.async (zero-filled outside the grid) FWD_WPD, ADJ_WPD
 //     or BORN_WPD rows ahead.
 //   - Element-wise updates and z-stencils use packed FP32x2 arithmetic.
@@ -22,7 +22,7 @@ namespace fwi {
 
 constexpr int WS = 120;    // columns owned by a warp
 constexpr int WH = 8;      // shared offset of column x0
-constexpr int WROW = 144;  // shared row: columns x0-8 .. x0+135
+constexpr int WROW = 136;  // shared row: columns x0-8 .. x0+127
 // rows each family prefetches ahead (measured on GB300: deeper staging costs shared memory,
 // hence resident warps; these depths balance the two)
 constexpr int FWD_WPD = 3;
