@@ -762,6 +762,7 @@ namespace fwi_internal {
 void set_error(const char *msg) { g_err = msg ? msg : ""; }
 }
 
+#include "fwi_arena.h"
 #include "fwi_engine.inc"
 
 extern "C" {
