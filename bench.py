@@ -25,6 +25,9 @@ Two more workloads run through the batching engine (one JSON line each, 1 GPU):
   --workload serve : a seeded Poisson stream of mixed forward / Born / gradient requests with
                      continuous batching; throughput and p50/p99 latency, against serving the
                      same stream one request at a time through the single-job calls.
+  --workload differentiation : one FWI gradient through torch.autograd on the 1201 x 1201,
+                     6000-step, 16-shot smooth-background workload with checkpoints every 200
+                     steps (per step: forward, torch misfit, backward).
 """
 from __future__ import annotations
 
@@ -95,7 +98,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="gradient workspace budget (0: 80%% of free device memory)")
-    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "batch", "serve"])
+    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "batch", "serve", "differentiation"])
     ap.add_argument("--jobs", type=int, default=256, help="batch: number of jobs")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
@@ -222,7 +225,8 @@ def main():
         return
     if args.workload != "gaussian":
         from paper_1804_01184_gb300 import workloads
-        (workloads.bench_batch if args.workload == "batch" else workloads.bench_serve)(args, Clocks)
+        {"batch": workloads.bench_batch, "serve": workloads.bench_serve,
+         "differentiation": workloads.bench_differentiation}[args.workload](args, Clocks)
         return
     import numpy as np
     import torch

@@ -21,6 +21,10 @@ from . import fwi
 class FwiFunction(torch.autograd.Function):
     """traces = F(xi_a, xi_b) for fixed grid, parameterization and acquisition."""
 
+    # library kernels launched by the most recent backward (autograd may run the backward on
+    # its own thread, where the library's per-thread launch counter lives)
+    last_backward_launches = 0
+
     @staticmethod
     def forward(ctx, xi_a, xi_b, grid, pz, src_xy, wavelet, rec_xy, budget_bytes):
         traces = fwi.fwi_model(grid, pz, xi_a.detach(), xi_b.detach(), src_xy, wavelet, rec_xy)
@@ -36,6 +40,7 @@ class FwiFunction(torch.autograd.Function):
         work = fwi.workspace(g, ns, nr, fwi.OP_ADJOINT, ctx.budget)
         G = fwi.fwi_adjoint(g, ctx.pz, xi_a, xi_b, src_xy, wavelet, rec_xy,
                             grad_traces.contiguous().float(), work=work)
+        FwiFunction.last_backward_launches = fwi.launch_count()
         ga = G[ctx.pz, 0].to(xi_a.dtype) if ctx.needs_input_grad[0] else None
         gb = G[ctx.pz, 1].to(xi_b.dtype) if ctx.needs_input_grad[1] else None
         return ga, gb, None, None, None, None, None, None

@@ -1,6 +1,6 @@
-"""Batching and serving workloads measured through the engine (bench.py --workload batch|serve).
+"""Batching, serving and differentiation workloads (bench.py --workload batch|serve|differentiation).
 
-Both print one JSON line.  Cell-updates count computational cells (sponge included) x steps
+Each prints one JSON line.  Cell-updates count computational cells (sponge included) x steps
 x shots x propagation passes: forward modelling 1, Born 2 (background and scattered
 fields), gradient 2 (forward and adjoint; recomputed forward steps are not counted).
 """
@@ -235,4 +235,64 @@ def bench_serve(args, Clocks):
                                     **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in st2.items()}}
     if prof:
         out["profile"] = prof
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------- differentiation
+
+def bench_differentiation(args, Clocks):
+    """One FWI gradient through torch.autograd on the 1201 x 1201 smooth-background workload
+    (6000 steps, 16 shots): forward modelling, a torch misfit, and the backward pass (adjoint
+    with wavefield checkpoints every 200 steps and segment recomputation)."""
+    from . import autograd as AG
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w, (a_bg, b_bg) = I.config_smooth()
+    g = grid_of(w)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    src, rec, wav = d(w.src_xy), d(w.rec_xy), d(w.wavelet)
+    data = F.fwi_model(g, w.pz, d(w.xi_a), d(w.xi_b), src, wav, rec)
+    F.fwi_set_checkpoint(200)
+    launches = [0]
+
+    def step():
+        a0 = d(a_bg).requires_grad_()
+        b0 = d(b_bg).requires_grad_()
+        tr = AG.model(a0, b0, g, w.pz, src, wav, rec)
+        launches[0] += F.launch_count()
+        J = 0.5 * ((tr.double() - data.double()) ** 2).sum()
+        J.backward()
+        launches[0] += AG.FwiFunction.last_backward_launches
+        return J, a0.grad, b0.grad
+
+    try:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = Clocks(0)
+        clocks.start()
+        launches[0] = 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            J, ga, gb = step()
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    finally:
+        F.fwi_set_checkpoint(0)
+    ms = e0.elapsed_time(e1) / args.steps
+    upd = 3 * cells(w)          # forward + (forward history + adjoint); recomputation not counted
+    out = {
+        "metric": METRIC, "value": round(upd / (ms / 1e3) / 1e9, 3), "unit": "Gcell-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "gradients_per_s": round(1e3 / ms, 4),
+        "config": {"workload": "smooth-1201x1201-o8 (autograd, checkpoints every 200 steps)",
+                   "grid": "1201x1201 + 40-cell sponge = 1281x1281", "nt": w.nt, "shots": w.ns, "receivers": w.nr,
+                   "step": "traces = FwiFunction(xi_a, xi_b); J = 1/2 |traces - data|^2 (torch); J.backward()",
+                   "passes": "forward 1 + backward (forward with checkpoints 1, recompute 1, adjoint 1)"},
+        "misfit": float(J.item()), "gradient_finite": bool(torch.isfinite(ga).all() and torch.isfinite(gb).all()),
+        "gpu_launches": launches[0] // max(args.steps, 1), "clocks": clk,
+    }
     print(json.dumps(out), flush=True)
