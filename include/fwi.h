@@ -237,7 +237,8 @@ int fwi_engine_submit(fwi_engine *engine, const fwi_job *job, long long *ticket)
  * running, the call waits for the GPU to finish the outstanding ones.  A call first waits
  * for the GPU to finish the work of the call before the previous one, so the host never
  * runs more than one call's iterations ahead of the GPU (what bounds the wait of a job
- * submitted between calls). */
+ * submitted between calls).  Returns FWI_OK or the first failure (FWI_ECUDA, ...) of the work
+ * it enqueued; after a failure the engine's jobs are undefined: destroy it. */
 int fwi_engine_run(fwi_engine *engine, int iterations, long long *done, int max_done, int *ndone);
 
 /* Jobs queued, running (admitted, not retired) and retired but not yet reported as done;

@@ -180,3 +180,28 @@ def test_invalid_jobs_are_refused(L):
     assert e.value.code == -3
     assert E.info() == dict(queued=0, running=0, pending=0, arena_used=0)
     E.close()
+
+
+def test_degenerate_jobs_and_a_job_filling_the_arena(L):
+    """Jobs without receivers or without shots finish with the single calls' results; a job
+    whose workspace is the whole arena waits until the jobs ahead of it retire, then runs."""
+    F, Eng = L
+    w = I.small_case(seed=500, nx=40, nz=36, nt=70, order=8, sponge=4, ns=2, nr=3)
+    g = gpu_grid(w)
+    none = np.zeros((0, 2), np.float32)
+    big = I.small_case(seed=501, nx=90, nz=80, nt=90, order=4, sponge=6, ns=3, nr=4)
+    data = I.random_like((big.ns, big.nr, big.nt), 502, 1e-3)
+    need = F.fwi_workspace_bytes(gpu_grid(big), big.ns, big.nr, F.OP_GRADIENT, 0)
+    E = Eng.Engine(need)
+    t_norec = E.submit_model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, none)
+    t_nosrc = E.submit_gradient(g, w.pz, w.xi_a, w.xi_b, none, w.wavelet, w.rec_xy,
+                                np.zeros((0, w.nr, w.nt), np.float32))
+    t_big = E.submit_gradient(gpu_grid(big), big.pz, big.xi_a, big.xi_b, big.src_xy, big.wavelet, big.rec_xy, data)
+    E.run(1)
+    assert E.info()["queued"] >= 1                     # the big job waits for the arena
+    res = {r.ticket: r for r in E.drain()}
+    assert res[t_norec].traces.shape == (w.ns, 0, w.nt)
+    torch.cuda.synchronize()
+    assert res[t_nosrc].misfit.item() == 0.0 and not torch.any(res[t_nosrc].grads != 0)
+    assert_same(outputs(res[t_big]), single(F, "gradient", big, {"data": data}, 0))
+    E.close()
