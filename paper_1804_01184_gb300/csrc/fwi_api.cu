@@ -528,10 +528,19 @@ StripTuner::Slot tuned_height(int fixed, const void *kernel, const fwi::Dims &d,
     return g_tuner.pick(key, s.tz, st);
 }
 
-// Warp-strip launch shape: one warp per (120-column strip, tz-row strip, shot), wpb warps a block.
-dim3 warp_grid(const Plan &P, int tz, int shots, int wpb = 2)
+// Warp-strip launch shape: one warp per (120-column strip, tz-row strip, shot), then
+// `extra` sampling warps, wpb warps a block.
+dim3 warp_grid(const Plan &P, int tz, int shots, int wpb = 2, int extra = 0)
 {
-    return dim3((unsigned)(((long long)fwi::strip_warps(P.d, tz, shots) + wpb - 1) / wpb));
+    return dim3((unsigned)(((long long)fwi::strip_warps(P.d, tz, shots) + extra + wpb - 1) / wpb));
+}
+
+// Sampling of the previous step carried by a single-job launch (none: count 0).
+fwi::Tail tail_of(const Plan &P, void *work, const float *field, float *traces, int bg, int col)
+{
+    const bool on = traces && field && P.nr > 0 && bg > 0 && col >= 0;
+    return fwi::Tail{field, traces, at<long long>(work, P.ridx), at<float>(work, P.rw), P.d.Np, P.nr, P.nt, col,
+                     on ? bg * P.nr : 0};
 }
 
 fwi::Model model_of(const Plan &P, void *work)
@@ -548,7 +557,8 @@ struct Fwd {
 
     // one forward step n for the group's shots [s0, s0 + bg): p^n in p0 -> p^{n+1} in p1,
     // velocities ping-pong on the parity of n
-    void step(int n, int s0, int bg, const float *p0, float *p1) const
+    // tl: sampling of the previous step by extra warps of this launch (count 0: none)
+    void step(int n, int s0, int bg, const float *p0, float *p1, const fwi::Tail &tl = fwi::Tail{}) const
     {
         const fwi::Dims &d = P.d;
         const fwi::Source src{at<long long>(work, P.sidx) + 4LL * s0, at<float>(work, P.sw) + 4LL * s0, wav};
@@ -560,20 +570,20 @@ struct Fwd {
         StripTuner::Key key;
         StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, T, S), st, key);
         const int tz = ts.tz;
-        const dim3 grid = warp_grid(P, tz, bg, fwi::FWD_WPB);
+        const dim3 grid = warp_grid(P, tz, bg, fwi::FWD_WPB, fwi::tail_warps(tl));
         const fwi::FwdArgs args{p0, vx0, vz0, p1, vx1, vz1, model_of(P, work), d, P.st, src, n, tz, bg};
         constexpr int B128 = fwi::minb(128, T), B170 = fwi::minb(170, T);
         if (P.M == 2) {
             switch (P.variant) {
-            case 1: SLAUNCH((fwi::k_fwd_warp<2, B128>), grid, T, S, st, args); break;
-            case 2: SLAUNCH((fwi::k_fwd_warp<2, B170>), grid, T, S, st, args); break;
-            default: SLAUNCH((fwi::k_fwd_warp<2, 1>), grid, T, S, st, args);
+            case 1: SLAUNCH((fwi::k_fwd_warp<2, B128>), grid, T, S, st, args, tl); break;
+            case 2: SLAUNCH((fwi::k_fwd_warp<2, B170>), grid, T, S, st, args, tl); break;
+            default: SLAUNCH((fwi::k_fwd_warp<2, 1>), grid, T, S, st, args, tl);
             }
         } else {
             switch (P.variant) {
-            case 1: SLAUNCH((fwi::k_fwd_warp<4, B128>), grid, T, S, st, args); break;
-            case 2: SLAUNCH((fwi::k_fwd_warp<4, B170>), grid, T, S, st, args); break;
-            default: SLAUNCH((fwi::k_fwd_warp<4, 1>), grid, T, S, st, args);
+            case 1: SLAUNCH((fwi::k_fwd_warp<4, B128>), grid, T, S, st, args, tl); break;
+            case 2: SLAUNCH((fwi::k_fwd_warp<4, B170>), grid, T, S, st, args, tl); break;
+            default: SLAUNCH((fwi::k_fwd_warp<4, 1>), grid, T, S, st, args, tl);
             }
         }
         g_tuner.finish(key, ts, st);
@@ -628,10 +638,10 @@ int forward_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
             CK(cudaMemcpyAsync(ck + slot, at<float>(work, P.vx[n & 1]), bf, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(ck + 2 * slot, at<float>(work, P.vz[n & 1]), bf, cudaMemcpyDeviceToDevice, st));
         }
-        float *p1 = pbuf(n + 1);
-        f.step(n, s0, bg, pbuf(n), p1);
-        if (traces) f.sample(n, bg, P.nr, p1, traces);
+        // this launch's extra warps sample p^n (the previous step's output) into column n - 1
+        f.step(n, s0, bg, pbuf(n), pbuf(n + 1), tail_of(P, work, pbuf(n), traces, bg, n - 1));
     }
+    if (traces && P.nt > 0) f.sample(P.nt - 1, bg, P.nr, pbuf(P.nt), traces);   // the last sample
     return FWI_OK;
 }
 
@@ -834,23 +844,24 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
             StripTuner::Key key;
             StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, 32, S), st, key);
             const int tz = ts.tz;
-            const dim3 grid = warp_grid(P, tz, bg, 1);
+            const fwi::Tail tl = tail_of(P, work, F(P.dp), out, bg, n - 1);   // samples q^n into column n - 1
+            const dim3 grid = warp_grid(P, tz, bg, 1, fwi::tail_warps(tl));
 #define BORN_ARGS fwi::BornArgs{F(P.p), F(P.vx), F(P.vz), F(P.dp), F(P.dvx), F(P.dvz), G(P.p), G(P.vx), \
                   G(P.vz), G(P.dp), G(P.dvx), G(P.dvz), mo, pe, d, P.st, sr, n, tz, bg}
             constexpr int B170 = fwi::minb(170, 32);
             if (P.M == 2) {
-                if (P.variant == 2) SLAUNCH((fwi::k_born_warp<2, B170>), grid, 32, S, st, BORN_ARGS);
-                else SLAUNCH((fwi::k_born_warp<2, 1>), grid, 32, S, st, BORN_ARGS);
+                if (P.variant == 2) SLAUNCH((fwi::k_born_warp<2, B170>), grid, 32, S, st, BORN_ARGS, tl);
+                else SLAUNCH((fwi::k_born_warp<2, 1>), grid, 32, S, st, BORN_ARGS, tl);
             } else {
-                if (P.variant == 2) SLAUNCH((fwi::k_born_warp<4, B170>), grid, 32, S, st, BORN_ARGS);
-                else SLAUNCH((fwi::k_born_warp<4, 1>), grid, 32, S, st, BORN_ARGS);
+                if (P.variant == 2) SLAUNCH((fwi::k_born_warp<4, B170>), grid, 32, S, st, BORN_ARGS, tl);
+                else SLAUNCH((fwi::k_born_warp<4, 1>), grid, 32, S, st, BORN_ARGS, tl);
             }
             g_tuner.finish(key, ts, st);
 #undef BORN_ARGS
-            if (P.nr > 0)
-                LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, G(P.dp), bg, P.nr, P.nt, n, d.Np,
-                       at<long long>(work, P.ridx), at<float>(work, P.rw), out);
         }
+        if (P.nr > 0 && P.nt > 0)   // the last sample: q^{nt}
+            LAUNCH(fwi::k_sample, (bg * P.nr + 127) / 128, 128, 0, st, at<float>(work, P.dp[P.nt & 1]), bg, P.nr,
+                   P.nt, P.nt - 1, d.Np, at<long long>(work, P.ridx), at<float>(work, P.rw), out);
     }
     return finish(st);
 }

@@ -162,6 +162,33 @@ __device__ __forceinline__ bool strip_has_src(const SrcCells &sc, int x0, int z0
 
 __device__ __forceinline__ float4 ldg_if(const float *p, bool v) { return v ? ldg4(p) : f4(0.f); }
 
+// Trace sampling of the PREVIOUS step carried by a single-job launch: the launch reads that
+// step's field (p^n, or the scattered q^n) only as its input, so extra warps appended to the
+// grid can sample it while the strips compute the next step; one launch fewer per step.
+// trace[s][r][n - 1] = sum_c beta_rc field[cell_rc], in the same corner order as k_sample.
+struct Tail {
+    const float *field;           // [shots][Np] the launch's input field
+    float *traces;                // [shots][nr][nt]
+    const long long *ridx;
+    const float *rw;
+    long long Np;
+    int nr, nt, col;              // col: trace sample written (n - 1)
+    int count;                    // shots x nr (0: no sampling)
+};
+
+__device__ __forceinline__ void sample_tail(const Tail &tl, int t)
+{
+    if (t >= tl.count) return;
+    const int s = t / tl.nr, r = t - s * tl.nr;
+    const float *ps = tl.field + (long long)s * tl.Np;
+    float v = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v += tl.rw[4 * r + c] * ps[tl.ridx[4 * r + c]];
+    tl.traces[(long long)t * tl.nt + tl.col] = v;
+}
+
+__host__ __device__ __forceinline__ int tail_warps(const Tail &tl) { return (tl.count + 31) / 32; }
+
 // ------------------------------------------------------------------ forward step (S3)
 //
 //   v^{n+1/2} = d_v (v^{n-1/2} - dt b D+ p^n);  p^{n+1} = d_p (p^n - dt K D-.v^{n+1/2}) + dt K w_n beta/dx^2
@@ -291,12 +318,16 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
 constexpr int minb(int regs, int threads) { return 65536 / (regs * threads); }
 
 template <int M, int MINB>
-__global__ void __launch_bounds__(32 * FWD_WPB, MINB) k_fwd_warp(FwdArgs a)
+__global__ void __launch_bounds__(32 * FWD_WPB, MINB) k_fwd_warp(FwdArgs a, Tail tl)
 {
     extern __shared__ __align__(16) unsigned char fwi_smem[];
+    const int w = blockIdx.x * FWD_WPB + (threadIdx.x >> 5), nw = strip_warps(a.d, a.tz, a.nshots);
+    if (w >= nw) {   // a sampling warp
+        sample_tail(tl, (w - nw) * 32 + (threadIdx.x & 31));
+        return;
+    }
     bool valid;
-    const Strip sp = strip_of(a.d, a.tz, a.nshots, FWD_WPB, valid);
-    if (!valid) return;
+    const Strip sp = strip_at(w, a.d, a.tz, a.nshots, valid);
     fwd_body<M>(a, sp, reinterpret_cast<FwdSmem<M> *>(fwi_smem)[threadIdx.x >> 5]);
 }
 
@@ -689,12 +720,16 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
 }
 
 template <int M, int MINB>
-__global__ void __launch_bounds__(32, MINB) k_born_warp(BornArgs a)
+__global__ void __launch_bounds__(32, MINB) k_born_warp(BornArgs a, Tail tl)
 {
     extern __shared__ __align__(16) unsigned char fwi_smem[];
+    const int w = blockIdx.x, nw = strip_warps(a.d, a.tz, a.nshots);
+    if (w >= nw) {   // a sampling warp
+        sample_tail(tl, (w - nw) * 32 + (threadIdx.x & 31));
+        return;
+    }
     bool valid;
-    const Strip sp = strip_of(a.d, a.tz, a.nshots, 1, valid);
-    if (!valid) return;
+    const Strip sp = strip_at(w, a.d, a.tz, a.nshots, valid);
     born_body<M>(a, sp, *reinterpret_cast<BornSmem<M> *>(fwi_smem));
 }
 
