@@ -331,13 +331,87 @@ __global__ void __launch_bounds__(32 * FWD_WPB, MINB) k_fwd_warp(FwdArgs a, Tail
     fwd_body<M>(a, sp, reinterpret_cast<FwdSmem<M> *>(fwi_smem)[threadIdx.x >> 5]);
 }
 
-// One time step of several independent jobs: warp w runs strip (w - wstart[j]) of job j.
+// Per-receiver work of the batching engine that rides on a batched forward launch after its
+// strips: trace samples of the previous engine iteration's steps (their fields are final and
+// only read in this launch) and this iteration's adjoint injections (their fields are read
+// by a later launch).  Thread u of the tail takes sample unit u, then injection units.
+struct SampleItem {
+    const float *p;            // p^{n+1} (or q^{n+1}) of the job's group
+    float *traces;             // [bg][nr][nt] of the group
+    const long long *ridx;
+    const float *rw;
+    long long Np;
+    int bg, nr, nt, n;
+};
+
+struct InjectItem {
+    float *ap, *accK;
+    const float *pn1, *res;
+    const long long *ridx;
+    const float *rw;
+    const int *rl;
+    long long Np;
+    int bg, nr, nt, n;
+};
+
+constexpr int SMALL_CAP = 40;
+
+struct SmallTable {
+    int nsmp, ninj;
+    int smp_start[SMALL_CAP + 1];     // prefix counts of units (threads)
+    int inj_start[SMALL_CAP + 1];
+    SampleItem smp[SMALL_CAP];
+    InjectItem inj[SMALL_CAP];
+};
+
+// defined with the adjoint kernels below
+__device__ __forceinline__ void inject_entry(float *__restrict__ ap, float *__restrict__ accK,
+                                             const float *__restrict__ pn1, int s, int k, int nr, int nt, int n,
+                                             long long Np, const long long *__restrict__ ridx,
+                                             const float *__restrict__ rw, const int *__restrict__ rl,
+                                             const float *__restrict__ res);
+
+__device__ __forceinline__ int small_units(const SmallTable &s) { return s.smp_start[s.nsmp] + s.inj_start[s.ninj]; }
+
+__device__ __forceinline__ void small_work(const SmallTable &s, int u)
+{
+    const int ns = s.smp_start[s.nsmp];
+    int l;
+    if (u < ns) {
+        const SampleItem &d = s.smp[job_of(u, s.smp_start, s.nsmp, l)];
+        const int sh = l / d.nr, r = l - sh * d.nr;
+        const float *ps = d.p + (long long)sh * d.Np;
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v += d.rw[4 * r + c] * ps[d.ridx[4 * r + c]];
+        d.traces[(long long)l * d.nt + d.n] = v;
+        return;
+    }
+    u -= ns;
+    if (u >= s.inj_start[s.ninj]) return;
+    const InjectItem &d = s.inj[job_of(u, s.inj_start, s.ninj, l)];
+    const int sh = l / (4 * d.nr);
+    inject_entry(d.ap, d.accK, d.pn1, sh, l - sh * 4 * d.nr, d.nr, d.nt, d.n, d.Np, d.ridx, d.rw, d.rl, d.res);
+}
+
+// A launch of per-receiver work alone (when no forward launch can carry it).
+__global__ void k_small_batch(const __grid_constant__ SmallTable s)
+{
+    small_work(s, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// One time step of several independent jobs: warp w runs strip (w - wstart[j]) of job j;
+// the warps after the strips do the per-receiver work of table s.
 template <int M>
-__global__ void __launch_bounds__(32 * FWD_WPB) k_fwd_batch(const __grid_constant__ BatchTable<FwdArgs> t)
+__global__ void __launch_bounds__(32 * FWD_WPB) k_fwd_batch(const __grid_constant__ BatchTable<FwdArgs> t,
+                                                          const __grid_constant__ SmallTable s)
 {
     extern __shared__ __align__(16) unsigned char fwi_smem[];
     const int w = blockIdx.x * FWD_WPB + (threadIdx.x >> 5);
-    if (w >= t.wstart[t.njobs]) return;
+    if (w >= t.wstart[t.njobs]) {
+        small_work(s, (w - t.wstart[t.njobs]) * 32 + (threadIdx.x & 31));
+        return;
+    }
     int local;
     const FwdArgs &a = t.jobs[job_of(w, t.wstart, t.njobs, local)];
     bool valid;
@@ -758,6 +832,8 @@ constexpr size_t born_smem() { return sizeof(BornSmem<M>); }
 static_assert(fwd_smem<4>() <= 227 * 1024 && adj_smem<4>() <= 227 * 1024 && born_smem<4>() <= 227 * 1024,
               "staging exceeds the shared memory of a block");
 
+static_assert(sizeof(BatchTable<FwdArgs>) + sizeof(SmallTable) <= 32000,
+              "forward batch and per-receiver tables exceed the kernel parameter space");
 static_assert(sizeof(BatchTable<FwdArgs>) <= 32000 && sizeof(BatchTable<AdjArgs>) <= 32000 &&
                   sizeof(BatchTable<BornArgs>) <= 32000,
               "batch table exceeds the kernel parameter space");
