@@ -205,3 +205,21 @@ def test_degenerate_jobs_and_a_job_filling_the_arena(L):
     assert res[t_nosrc].misfit.item() == 0.0 and not torch.any(res[t_nosrc].grads != 0)
     assert_same(outputs(res[t_big]), single(F, "gradient", big, {"data": data}, 0))
     E.close()
+
+
+def test_many_gradients_overflow_the_per_receiver_table(L):
+    """More adjoint jobs than one forward launch's per-receiver table holds (40): the rest of
+    the injections go out in their own launches; every result equals the single call."""
+    F, Eng = L
+    E = Eng.Engine(2 << 30)
+    jobs = []
+    for s in range(56):
+        case = dict(seed=600 + s, nx=26 + s % 5, nz=22 + s % 3, nt=24 + s % 7, order=8, sponge=3, ns=1 + s % 2,
+                    nr=3, pz=s % 5)
+        jobs.append(("gradient", *make_inputs("gradient", case), 0))
+    jobs.append(("model", *make_inputs("model", dict(seed=700, nx=30, nz=30, nt=60, ns=2, nr=3)), 0))
+    tickets = [submit(E, k, w, x, b) for k, w, x, b in jobs]
+    res = {r.ticket: r for r in E.drain()}
+    for t, (k, w, x, b) in zip(tickets, jobs):
+        assert_same(outputs(res[t]), single(F, k, w, x, b))
+    E.close()

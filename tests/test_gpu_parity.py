@@ -307,3 +307,27 @@ def test_strip_heights_give_bitwise_identical_results(F):
         np.testing.assert_array_equal(o[1], out[0][1])
         assert o[2] == out[0][2]
         np.testing.assert_array_equal(o[3], out[0][3])
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_register_capped_variants_are_bitwise_identical(F, variant):
+    """The register-capped builds of the streaming kernels (fwi_set_tile's variant) compute
+    the same arithmetic: traces, Born traces and gradients equal the default build bitwise."""
+    w = I.small_case(seed=24, nx=64, nz=58, nt=110, order=8, sponge=6, ns=2, nr=5)
+    g = gpu_grid(w)
+    da, db = I.random_like(w.xi_a.shape, 6, 0.05), I.random_like(w.xi_a.shape, 7, 0.05)
+    data = I.random_like((w.ns, w.nr, w.nt), 8, 1e3)
+    out = []
+    try:
+        for v in (0, variant):
+            F.fwi_set_tile(0, v)
+            tr = run_model(F, w)
+            bo = F.fwi_born(g, w.pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy).cpu().numpy()
+            J, G = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, data)
+            out.append((tr, bo, J.item(), G.cpu().numpy()))
+    finally:
+        F.fwi_set_tile(0, 0)
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    np.testing.assert_array_equal(out[1][1], out[0][1])
+    assert out[1][2] == out[0][2]
+    np.testing.assert_array_equal(out[1][3], out[0][3])
