@@ -25,6 +25,8 @@ Two more workloads run through the batching engine (one JSON line each, 1 GPU):
   --workload serve : a seeded Poisson stream of mixed forward / Born / gradient requests with
                      continuous batching; throughput and p50/p99 latency, against serving the
                      same stream one request at a time through the single-job calls.
+  --workload bowls : error bowls of a known-shape scatterer in all five parameterizations
+                     (2205 forward solves through the batching engine).
   --workload differentiation : one FWI gradient through torch.autograd on the 1201 x 1201,
                      6000-step, 16-shot smooth-background workload with checkpoints every 200
                      steps (per step: forward, torch misfit, backward).
@@ -98,7 +100,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="gradient workspace budget (0: 80%% of free device memory)")
-    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "batch", "serve", "differentiation"])
+    ap.add_argument("--workload", default="gaussian",
+                    choices=["gaussian", "batch", "serve", "differentiation", "bowls"])
+    ap.add_argument("--case", default="ii", choices=["i", "ii", "iv", "v"], help="bowls: scatterer")
+    ap.add_argument("--bowl-n", type=int, default=21, help="bowls: contrasts per axis")
     ap.add_argument("--jobs", type=int, default=256, help="batch: number of jobs")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
@@ -226,7 +231,7 @@ def main():
     if args.workload != "gaussian":
         from paper_1804_01184_gb300 import workloads
         {"batch": workloads.bench_batch, "serve": workloads.bench_serve,
-         "differentiation": workloads.bench_differentiation}[args.workload](args, Clocks)
+         "differentiation": workloads.bench_differentiation, "bowls": workloads.bench_bowls}[args.workload](args, Clocks)
         return
     import numpy as np
     import torch

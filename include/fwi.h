@@ -127,6 +127,12 @@ int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float
                  const fwi_sources *src, const fwi_receivers *rec, const float *data,
                  double *misfit, double *grads, void *work, size_t work_bytes, void *stream);
 
+/* Least-squares misfit of one set of traces (Sec. "Modelling and Inversion"): writes
+ * J = 1/2 sum_k (traces[k] - data[k])^2, accumulated in FP64 in a fixed order, to *misfit
+ * (device, 1 float64).  traces, data: `count` float32 values (device).  Allocates nothing;
+ * asynchronous on `stream`.  Used for misfit surfaces over many forward models (error bowls). */
+int fwi_misfit(const float *traces, const float *data, long long count, double *misfit, void *stream);
+
 /* Waits for `stream` and returns the data-dependent status recorded by the last operation
  * that used `work` (FWI_OK, FWI_EINVAL, FWI_ECFL), then clears it. */
 int fwi_status(void *work, void *stream);

@@ -914,6 +914,16 @@ int fwi_status(void *work, void *stream)
 
 const char *fwi_last_error(void) { return g_err.c_str(); }
 
+int fwi_misfit(const float *traces, const float *data, long long count, double *misfit, void *stream)
+{
+    g_err.clear();
+    g_launches = 0;
+    if (count < 0 || !misfit || (count > 0 && (!traces || !data))) return fail(FWI_EINVAL, "invalid misfit arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LAUNCH(fwi::k_misfit, 1, fwi::RED_THREADS, 0, st, traces, data, count, misfit);
+    return finish(st);
+}
+
 
 int fwi_set_checkpoint(int every)
 {

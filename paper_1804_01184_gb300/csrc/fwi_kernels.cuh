@@ -250,6 +250,20 @@ __device__ __forceinline__ double block_sum(double v)
 }
 
 // r = traces - data (in place in `tr`), partial[blockIdx.x] = 1/2 sum r^2 (FP64).
+// J = 1/2 sum (tr - data)^2 in FP64 by one block (a fixed summation order, no scratch): the
+// least-squares misfit of one set of traces (Sec. "Modelling and Inversion").
+__global__ void __launch_bounds__(RED_THREADS) k_misfit(const float *__restrict__ tr, const float *__restrict__ data,
+                                                       long long n, double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (long long k = threadIdx.x; k < n; k += RED_THREADS) {
+        const double r = (double)tr[k] - (double)data[k];
+        acc += 0.5 * r * r;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = acc;
+}
+
 __global__ void __launch_bounds__(RED_THREADS) k_residual(float *__restrict__ tr, const float *__restrict__ data,
                                                           long long n, double *__restrict__ partial)
 {

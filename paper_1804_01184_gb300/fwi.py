@@ -75,6 +75,7 @@ def lib():
             L.fwi_adjoint.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, vp, C.c_size_t, vp]
             L.fwi_gradient.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, dp, vp, C.c_size_t, vp]
             L.fwi_status.argtypes = [vp, vp]
+            L.fwi_misfit.argtypes = [vp, vp, C.c_longlong, vp, vp]
             L.fwi_last_error.restype = C.c_char_p
             L.fwi_launch_count.restype = C.c_longlong
             L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
@@ -229,3 +230,14 @@ def fwi_gradient(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, data,
     if check:
         fwi_status(work, stream)
     return misfit, grads
+
+
+def fwi_misfit(traces, data, misfit=None, stream=None) -> torch.Tensor:
+    """J = 1/2 sum (traces - data)^2 (float64 device scalar tensor), in the library's kernel."""
+    t, d = _dev(traces), _dev(data)
+    if t.numel() != d.numel():
+        raise FwiError(-1, "traces and data differ in size")
+    if misfit is None:
+        misfit = torch.empty((), dtype=torch.float64, device="cuda")
+    _raise(lib().fwi_misfit(_ptr(t), _ptr(d), t.numel(), _ptr(misfit), _stream(stream)))
+    return misfit

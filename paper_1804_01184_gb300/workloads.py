@@ -1,4 +1,5 @@
-"""Batching, serving and differentiation workloads (bench.py --workload batch|serve|differentiation).
+"""Batching, serving, differentiation and error-bowl workloads
+(bench.py --workload batch|serve|differentiation|bowls).
 
 Each prints one JSON line.  Cell-updates count computational cells (sponge included) x steps
 x shots x propagation passes, as bench.py's default line does: forward modelling 1, Born 1
@@ -295,5 +296,49 @@ def bench_differentiation(args, Clocks):
                    "passes": "forward 1 + backward (forward with checkpoints 1, recompute 1, adjoint 1)"},
         "misfit": float(J.item()), "gradient_finite": bool(torch.isfinite(ga).all() and torch.isfinite(gb).all()),
         "gpu_launches": launches[0] // max(args.steps, 1), "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------ error bowls
+
+def bench_bowls(args, Clocks):
+    """Error bowls of scatterer `args.case` (paper acquisition, 121 x 121 + 40-cell sponge,
+    1400 steps, 10 shots, 100 receivers, 5 Hz) in all five parameterizations, 21 x 21 contrasts
+    each: 2205 forward solves through the batching engine."""
+    from . import bowls as B
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w, g = B.scatterer(args.case)
+    shape, which = B.CASES[args.case]
+    amp = 0.2
+    data = F.fwi_model(grid_of(w), I.PZ_VP_RHO, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    dvp, drho = (amp, 0.0) if which == "vp" else (0.0, amp)
+    grids = {}
+    for pz in range(5):
+        ta, tb = B.true_point(pz, dvp, drho)
+        grids[pz] = (B.grid_around(ta, args.bowl_n), B.grid_around(tb, args.bowl_n))
+    B.error_bowl(w, g, I.PZ_K_RHO, data, grids[I.PZ_K_RHO][0][:3], grids[I.PZ_K_RHO][1][:3])   # warm-up
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    shapes, launches = {}, 0
+    for pz in range(5):
+        J, l = B.error_bowl(w, g, pz, data, *grids[pz])
+        launches += l
+        shapes[["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"][pz]] = {
+            k: (round(v, 4) if isinstance(v, float) else [round(x, 4) for x in v]) for k, v in B.bowl_shape(J, *grids[pz]).items()}
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    solves = 5 * args.bowl_n ** 2
+    upd = solves * cells(w)
+    out = {
+        "metric": METRIC, "value": round(upd / wall / 1e9, 3), "unit": "Gcell-updates/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": round(1e3 * wall, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"bowls-scatterer-{args.case}", "scatterer": f"{shape}, {which} only, contrast {amp}",
+                   "grid": "121x121 + 40-cell sponge, dx 10 m, 8th order, 1400 steps, 10 shots, 100 receivers, 5 Hz",
+                   "bowl": f"{args.bowl_n}x{args.bowl_n} contrasts per parameterization, 5 parameterizations"},
+        "solves_per_s": round(solves / wall, 2), "bowls": shapes, "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(out), flush=True)

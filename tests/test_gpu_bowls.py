@@ -1,0 +1,56 @@
+"""Error bowls (Sec. "Error-bowl Analysis") through the batching engine: the misfit surface of
+a scatterer of known shape over a grid of its two contrasts.  The bowl is exactly zero at the
+true contrasts (same discrete model), its values match the FP64 oracle within the bound the
+trace tolerance implies, and fwi_misfit agrees with a float64 reduction."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_01184_gb300 import inputs as I
+from tests._common import TRACE_TOL, gpu_grid, oracle_grid
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_01184_gb300 import bowls, build, fwi
+    build.build()
+    return fwi, bowls
+
+
+def test_misfit_kernel_matches_float64(L):
+    F, _ = L
+    a = I.random_like((3, 17, 333), 1, 1.0)
+    b = I.random_like((3, 17, 333), 2, 1.0)
+    J = F.fwi_misfit(a, b).item()
+    ref = 0.5 * np.sum((a.astype(np.float64) - b.astype(np.float64)) ** 2)
+    assert abs(J - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("pz", [I.PZ_K_RHO, I.PZ_VP_IP])
+def test_bowl_zero_at_truth_and_oracle_values(L, pz):
+    F, B = L
+    w = I.small_case(seed=31, nx=50, nz=46, nt=160, order=8, sponge=6, ns=3, nr=8, pz=pz)
+    g = I.gaussian(w.nx, w.nz, w.dx, I.centre_of(w.nx, w.nz, w.dx), 15.0)
+    ga = np.array([-0.1, 0.0, 0.1, 0.2, 0.3], np.float32)
+    gb = np.array([-0.2, -0.1, 0.0, 0.1], np.float32)
+    ta, tb = 3, 1                                          # truth (0.2, -0.1)
+    w.xi_a, w.xi_b = g * ga[ta], g * gb[tb]
+    data = F.fwi_model(gpu_grid(w), pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    J, launches = B.error_bowl(w, g, pz, data, ga, gb, arena_bytes=1 << 30)
+    assert launches > 0
+    assert J[ta, tb] == 0.0 and np.unravel_index(int(np.argmin(J)), J.shape) == (ta, tb)
+    og = oracle_grid(w)
+    d_ref = oracle.model(og, pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    eb = 2 * TRACE_TOL * np.linalg.norm(d_ref)             # trace error of both sides
+    for ia, ib in [(0, 0), (4, 3), (1, 2), (3, 0)]:
+        tr = oracle.model(og, pz, g * ga[ia], g * gb[ib], w.src_xy, w.wavelet, w.rec_xy)
+        r = np.linalg.norm(tr - d_ref)
+        J_ref = 0.5 * r * r
+        assert abs(J[ia, ib] - J_ref) <= r * eb + 0.5 * eb * eb, (ia, ib, J[ia, ib], J_ref)
+    s = B.bowl_shape(J, ga, gb, half=1)
+    assert s["argmin"] == (float(ga[ta]), float(gb[tb])) and s["condition"] >= 1.0
