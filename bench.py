@@ -27,6 +27,8 @@ Two more workloads run through the batching engine (one JSON line each, 1 GPU):
                      same stream one request at a time through the single-job calls.
   --workload bowls : error bowls of a known-shape scatterer in all five parameterizations
                      (2205 forward solves through the batching engine).
+  --workload invert : steepest-descent inversions of a known-shape scatterer in all five
+                     parameterizations (line searches as engine jobs); misfit histories.
   --workload differentiation : one FWI gradient through torch.autograd on the 1201 x 1201,
                      6000-step, 16-shot smooth-background workload with checkpoints every 200
                      steps (per step: forward, torch misfit, backward).
@@ -101,7 +103,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="gradient workspace budget (0: 80%% of free device memory)")
     ap.add_argument("--workload", default="gaussian",
-                    choices=["gaussian", "batch", "serve", "differentiation", "bowls"])
+                    choices=["gaussian", "batch", "serve", "differentiation", "bowls", "invert"])
+    ap.add_argument("--iters", type=int, default=15, help="invert: iterations")
     ap.add_argument("--case", default="ii", choices=["i", "ii", "iv", "v"], help="bowls: scatterer")
     ap.add_argument("--bowl-n", type=int, default=21, help="bowls: contrasts per axis")
     ap.add_argument("--jobs", type=int, default=256, help="batch: number of jobs")
@@ -231,7 +234,8 @@ def main():
     if args.workload != "gaussian":
         from paper_1804_01184_gb300 import workloads
         {"batch": workloads.bench_batch, "serve": workloads.bench_serve,
-         "differentiation": workloads.bench_differentiation, "bowls": workloads.bench_bowls}[args.workload](args, Clocks)
+         "differentiation": workloads.bench_differentiation, "bowls": workloads.bench_bowls,
+         "invert": workloads.bench_invert}[args.workload](args, Clocks)
         return
     import numpy as np
     import torch

@@ -1,5 +1,5 @@
-"""Batching, serving, differentiation and error-bowl workloads
-(bench.py --workload batch|serve|differentiation|bowls).
+"""Batching, serving, differentiation, error-bowl and inversion workloads
+(bench.py --workload batch|serve|differentiation|bowls|invert).
 
 Each prints one JSON line.  Cell-updates count computational cells (sponge included) x steps
 x shots x propagation passes, as bench.py's default line does: forward modelling 1, Born 1
@@ -340,5 +340,41 @@ def bench_bowls(args, Clocks):
                    "grid": "121x121 + 40-cell sponge, dx 10 m, 8th order, 1400 steps, 10 shots, 100 receivers, 5 Hz",
                    "bowl": f"{args.bowl_n}x{args.bowl_n} contrasts per parameterization, 5 parameterizations"},
         "solves_per_s": round(solves / wall, 2), "bowls": shapes, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
+# -------------------------------------------------------------------------------- inversion
+
+def bench_invert(args, Clocks):
+    """Steepest descent with an engine-batched line search on scatterer `args.case` (known
+    shape: the two contrasts are the unknowns) in all five parameterizations, from the
+    homogeneous starting model; reports each misfit history (the convergence ranking)."""
+    from . import bowls as B
+    from . import invert as V
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w, g = B.scatterer(args.case)
+    data = F.fwi_model(grid_of(w), I.PZ_VP_RHO, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    names = ["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"]
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    res = {}
+    for pz in range(5):
+        inv = V.Inversion(w, pz, data, shape=g)
+        m, hist = inv.run((0.0, 0.0), iters=args.iters)
+        inv.close()
+        res[names[pz]] = {"final": [round(m[0], 5), round(m[1], 5)], "misfit": [float(f"{j:.5g}") for j in hist],
+                          "reduction": float(f"{hist[-1] / hist[0]:.4g}")}
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    out = {
+        "metric": METRIC, "value": round(wall, 2), "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": round(1e3 * wall, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"invert-scatterer-{args.case}-known-shape", "iterations": args.iters,
+                   "line_search": "8 trial steps a iteration as engine jobs"},
+        "inversions": res, "clocks": clk,
     }
     print(json.dumps(out), flush=True)
