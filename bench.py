@@ -107,6 +107,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=15, help="invert: iterations")
     ap.add_argument("--case", default="ii", choices=["i", "ii", "iv", "v"], help="bowls: scatterer")
     ap.add_argument("--bowl-n", type=int, default=21, help="bowls: contrasts per axis")
+    ap.add_argument("--aperture", default="all", choices=["all", "short", "long"],
+                    help="bowls: scattering angles used (short: 0-90, long: 135-180 degrees)")
     ap.add_argument("--jobs", type=int, default=256, help="batch: number of jobs")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")

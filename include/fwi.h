@@ -133,6 +133,20 @@ int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float
  * asynchronous on `stream`.  Used for misfit surfaces over many forward models (error bowls). */
 int fwi_misfit(const float *traces, const float *data, long long count, double *misfit, void *stream);
 
+/* fwi_gradient with a weight per trace: J = 1/2 sum_{s,r,n} w[s][r] (d_mod - data)^2, whose
+ * adjoint source is w (d_mod - data).  weights: [ns][nr] float32 (device), null = all 1 (then
+ * identical to fwi_gradient).  A 0/1 weight selects the traces of a limited aperture, e.g. a
+ * range of scattering angles (Sec. "Hierarchical Inversion"). */
+int fwi_gradient_weighted(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+                          const fwi_sources *src, const fwi_receivers *rec, const float *data,
+                          const float *weights, double *misfit, double *grads, void *work, size_t work_bytes,
+                          void *stream);
+
+/* fwi_misfit with a weight per trace: J = 1/2 sum_t w[t] sum_n (traces[t][n] - data[t][n])^2
+ * over ntraces traces of nt samples; weights null = all 1. */
+int fwi_misfit_weighted(const float *traces, const float *data, long long ntraces, int nt, const float *weights,
+                        double *misfit, void *stream);
+
 /* Waits for `stream` and returns the data-dependent status recorded by the last operation
  * that used `work` (FWI_OK, FWI_EINVAL, FWI_ECFL), then clears it. */
 int fwi_status(void *work, void *stream);

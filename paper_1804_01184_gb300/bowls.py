@@ -58,14 +58,32 @@ def grid_around(t, n=21, margin=1.0):
     return t + h * (np.arange(n) - m)
 
 
-def error_bowl(w, g, pz, data, grid_a, grid_b, arena_bytes=None, work_budget=1 << 30):
+def aperture_weights(src_xy, rec_xy, x0, lo_deg, hi_deg):
+    """[ns][nr] float32 weights selecting the traces whose scattering angle at x0 -- the angle
+    between the incident direction (source to x0) and the scattered one (x0 to receiver) --
+    lies in [lo_deg, hi_deg] (Sec. "Hierarchical Inversion": short offsets 0-90 degrees, long
+    offsets 135-180 degrees)."""
+    s = np.asarray(src_xy, np.float64).reshape(-1, 2)
+    r = np.asarray(rec_xy, np.float64).reshape(-1, 2)
+    x0 = np.asarray(x0, np.float64)
+    inc = x0 - s
+    sca = r - x0
+    inc /= np.linalg.norm(inc, axis=1, keepdims=True)
+    sca /= np.linalg.norm(sca, axis=1, keepdims=True)
+    ang = np.degrees(np.arccos(np.clip(inc @ sca.T, -1.0, 1.0)))
+    return ((ang >= lo_deg) & (ang <= hi_deg)).astype(np.float32)
+
+
+def error_bowl(w, g, pz, data, grid_a, grid_b, arena_bytes=None, work_budget=1 << 30, weights=None):
     """J[ia][ib] (float64 numpy) for contrasts (grid_a[ia] g, grid_b[ib] g) in parameterization
-    pz against observed traces `data`; every grid point is a job of one engine."""
+    pz against observed traces `data`; every grid point is a job of one engine.  weights:
+    optional [ns][nr] trace weights (e.g. aperture_weights)."""
     dev = torch.device("cuda")
     grid = F.make_grid(**w.grid_kwargs())
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     src, rec, wav, gg = d(w.src_xy), d(w.rec_xy), d(w.wavelet), d(g)
     obs = F._dev(data).reshape(-1)
+    wt = d(weights) if weights is not None else None
     if arena_bytes is None:
         free, _ = torch.cuda.mem_get_info()
         arena_bytes = int(free * 0.5) // 256 * 256
@@ -81,7 +99,7 @@ def error_bowl(w, g, pz, data, grid_a, grid_b, arena_bytes=None, work_budget=1 <
     while tick:
         for r in eng.run(64):
             ia, ib = tick.pop(r.ticket)
-            F.fwi_misfit(r.traces.reshape(-1), obs, misfit=J[ia, ib], stream=eng.stream)
+            F.fwi_misfit(r.traces.reshape(-1), obs, misfit=J[ia, ib], stream=eng.stream, weights=wt, nt=w.nt)
         launches += F.launch_count()
     torch.cuda.synchronize()
     eng.close()

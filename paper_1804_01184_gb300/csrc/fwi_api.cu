@@ -723,7 +723,7 @@ int finalize_grad(const Plan &P, const fwi_grid *g, int pz, const float *xa, con
 
 int adjoint_impl(const fwi_grid *g, int pz, const float *xa, const float *xb, const fwi_sources *src,
                  const fwi_receivers *rec, const float *residual, const float *data, double *misfit,
-                 double *grads, void *work, size_t work_bytes, cudaStream_t st)
+                 double *grads, void *work, size_t work_bytes, cudaStream_t st, const float *weights = nullptr)
 {
     const fwi_op op = data ? FWI_OP_GRADIENT : FWI_OP_ADJOINT;
     Plan P;
@@ -744,7 +744,8 @@ int adjoint_impl(const fwi_grid *g, int pz, const float *xa, const float *xb, co
             const long long n = bg * per_shot;
             if (n > 0)
                 LAUNCH(fwi::k_residual, RED_BLOCKS, fwi::RED_THREADS, 0, st, tr, data + s0 * per_shot, n,
-                       at<double>(work, P.partial) + (size_t)gi * RED_BLOCKS);
+                       at<double>(work, P.partial) + (size_t)gi * RED_BLOCKS,
+                       weights ? weights + (size_t)s0 * P.nr : nullptr, P.nt);
             else
                 CK(cudaMemsetAsync(at<double>(work, P.partial) + (size_t)gi * RED_BLOCKS, 0,
                                    RED_BLOCKS * sizeof(double), st));
@@ -881,9 +882,10 @@ int fwi_adjoint(const fwi_grid *g, fwi_param pz, const float *xi_a, const float 
                         static_cast<cudaStream_t>(stream));
 }
 
-int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b, const fwi_sources *src,
-                 const fwi_receivers *rec, const float *data, double *misfit, double *grads, void *work,
-                 size_t work_bytes, void *stream)
+int fwi_gradient_weighted(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
+                          const fwi_sources *src, const fwi_receivers *rec, const float *data,
+                          const float *weights, double *misfit, double *grads, void *work, size_t work_bytes,
+                          void *stream)
 {
     g_err.clear();
     g_launches = 0;
@@ -894,7 +896,15 @@ int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float
     if (src->ns > 0 && rec->nr > 0 && !data) return fail(FWI_EINVAL, "null data");
     static const float dummy = 0.f;
     return adjoint_impl(g, pz, xi_a, xi_b, src, rec, nullptr, data ? data : &dummy, misfit, grads, work,
-                        work_bytes, static_cast<cudaStream_t>(stream));
+                        work_bytes, static_cast<cudaStream_t>(stream), weights);
+}
+
+int fwi_gradient(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b, const fwi_sources *src,
+                 const fwi_receivers *rec, const float *data, double *misfit, double *grads, void *work,
+                 size_t work_bytes, void *stream)
+{
+    return fwi_gradient_weighted(g, pz, xi_a, xi_b, src, rec, data, nullptr, misfit, grads, work, work_bytes,
+                                 stream);
 }
 
 int fwi_status(void *work, void *stream)
@@ -914,14 +924,22 @@ int fwi_status(void *work, void *stream)
 
 const char *fwi_last_error(void) { return g_err.c_str(); }
 
-int fwi_misfit(const float *traces, const float *data, long long count, double *misfit, void *stream)
+int fwi_misfit_weighted(const float *traces, const float *data, long long ntraces, int nt, const float *weights,
+                        double *misfit, void *stream)
 {
     g_err.clear();
     g_launches = 0;
-    if (count < 0 || !misfit || (count > 0 && (!traces || !data))) return fail(FWI_EINVAL, "invalid misfit arguments");
+    if (ntraces < 0 || nt < 1 || !misfit || (ntraces > 0 && (!traces || !data)))
+        return fail(FWI_EINVAL, "invalid misfit arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LAUNCH(fwi::k_misfit, 1, fwi::RED_THREADS, 0, st, traces, data, count, misfit);
+    LAUNCH(fwi::k_misfit, 1, fwi::RED_THREADS, 0, st, traces, data, ntraces * nt, weights, nt, misfit);
     return finish(st);
+}
+
+int fwi_misfit(const float *traces, const float *data, long long count, double *misfit, void *stream)
+{
+    if (count < 0) return fail(FWI_EINVAL, "invalid misfit arguments");
+    return fwi_misfit_weighted(traces, data, count, 1, nullptr, misfit, stream);
 }
 
 

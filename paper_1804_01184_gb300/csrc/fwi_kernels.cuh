@@ -250,29 +250,40 @@ __device__ __forceinline__ double block_sum(double v)
 }
 
 // r = traces - data (in place in `tr`), partial[blockIdx.x] = 1/2 sum r^2 (FP64).
-// J = 1/2 sum (tr - data)^2 in FP64 by one block (a fixed summation order, no scratch): the
-// least-squares misfit of one set of traces (Sec. "Modelling and Inversion").
+// J = 1/2 sum w (tr - data)^2 in FP64 by one block (a fixed summation order, no scratch): the
+// least-squares misfit of one set of traces (Sec. "Modelling and Inversion"), each trace
+// (nt samples) weighted by w[trace] (w null: 1).
 __global__ void __launch_bounds__(RED_THREADS) k_misfit(const float *__restrict__ tr, const float *__restrict__ data,
-                                                       long long n, double *__restrict__ out)
+                                                       long long n, const float *__restrict__ w, int nt,
+                                                       double *__restrict__ out)
 {
     double acc = 0.0;
     for (long long k = threadIdx.x; k < n; k += RED_THREADS) {
         const double r = (double)tr[k] - (double)data[k];
-        acc += 0.5 * r * r;
+        acc += w ? 0.5 * (double)w[k / nt] * r * r : 0.5 * r * r;
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) *out = acc;
 }
 
+// Residual in place, tr <- w (tr - data), and per-block partial misfits 1/2 w (tr - data)^2:
+// the adjoint source of J = 1/2 sum w r^2 (w null: 1; w per trace of nt samples).
 __global__ void __launch_bounds__(RED_THREADS) k_residual(float *__restrict__ tr, const float *__restrict__ data,
-                                                          long long n, double *__restrict__ partial)
+                                                          long long n, double *__restrict__ partial,
+                                                          const float *__restrict__ w, int nt)
 {
     double acc = 0.0;
     for (long long k = (long long)blockIdx.x * RED_THREADS + threadIdx.x; k < n;
          k += (long long)gridDim.x * RED_THREADS) {
         const float r = tr[k] - data[k];
-        tr[k] = r;
-        acc += 0.5 * (double)r * (double)r;
+        if (w) {
+            const float wk = w[k / nt];
+            tr[k] = wk * r;
+            acc += 0.5 * (double)wk * (double)r * (double)r;
+        } else {
+            tr[k] = r;
+            acc += 0.5 * (double)r * (double)r;
+        }
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;

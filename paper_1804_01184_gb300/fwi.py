@@ -76,6 +76,8 @@ def lib():
             L.fwi_gradient.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, dp, vp, C.c_size_t, vp]
             L.fwi_status.argtypes = [vp, vp]
             L.fwi_misfit.argtypes = [vp, vp, C.c_longlong, vp, vp]
+            L.fwi_misfit_weighted.argtypes = [vp, vp, C.c_longlong, C.c_int, vp, vp, vp]
+            L.fwi_gradient_weighted.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp, dp, dp, vp, C.c_size_t, vp]
             L.fwi_last_error.restype = C.c_char_p
             L.fwi_launch_count.restype = C.c_longlong
             L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
@@ -215,8 +217,9 @@ def fwi_adjoint(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, residu
 
 
 def fwi_gradient(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, data, misfit=None, grads=None,
-                 work=None, stream=None, check=True):
-    """Misfit (device float64 scalar tensor) and gradients [5][2][nz][nx] float64."""
+                 work=None, stream=None, check=True, weights=None):
+    """Misfit (device float64 scalar tensor) and gradients [5][2][nz][nx] float64.  weights:
+    optional [ns][nr] per-trace weights (fwi_gradient_weighted)."""
     a, b, d = _dev(xi_a), _dev(xi_b), _dev(data)
     keep, S, R = _acq(src_xy, wavelet, rec_xy)
     if grads is None:
@@ -225,19 +228,35 @@ def fwi_gradient(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, data,
         misfit = torch.empty((), dtype=torch.float64, device="cuda")
     if work is None:
         work = workspace(grid, S.ns, R.nr, OP_GRADIENT)
-    _raise(lib().fwi_gradient(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(d),
-                              _ptr(misfit), _ptr(grads), _ptr(work), work.numel(), _stream(stream)))
+    if weights is None:
+        _raise(lib().fwi_gradient(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(d),
+                                  _ptr(misfit), _ptr(grads), _ptr(work), work.numel(), _stream(stream)))
+    else:
+        wt = _dev(weights)
+        if wt.numel() != S.ns * R.nr:
+            raise FwiError(-1, "weights must hold ns x nr values")
+        _raise(lib().fwi_gradient_weighted(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R),
+                                           _ptr(d), _ptr(wt), _ptr(misfit), _ptr(grads), _ptr(work), work.numel(),
+                                           _stream(stream)))
     if check:
         fwi_status(work, stream)
     return misfit, grads
 
 
-def fwi_misfit(traces, data, misfit=None, stream=None) -> torch.Tensor:
-    """J = 1/2 sum (traces - data)^2 (float64 device scalar tensor), in the library's kernel."""
+def fwi_misfit(traces, data, misfit=None, stream=None, weights=None, nt=None) -> torch.Tensor:
+    """J = 1/2 sum (traces - data)^2 (float64 device scalar tensor), in the library's kernel;
+    with weights (one per trace of nt samples), J = 1/2 sum_t w_t sum_n (...)^2."""
     t, d = _dev(traces), _dev(data)
     if t.numel() != d.numel():
         raise FwiError(-1, "traces and data differ in size")
     if misfit is None:
         misfit = torch.empty((), dtype=torch.float64, device="cuda")
-    _raise(lib().fwi_misfit(_ptr(t), _ptr(d), t.numel(), _ptr(misfit), _stream(stream)))
+    if weights is None:
+        _raise(lib().fwi_misfit(_ptr(t), _ptr(d), t.numel(), _ptr(misfit), _stream(stream)))
+    else:
+        wt = _dev(weights)
+        if nt is None or wt.numel() * nt != t.numel():
+            raise FwiError(-1, "weights x nt must cover the traces")
+        _raise(lib().fwi_misfit_weighted(_ptr(t), _ptr(d), wt.numel(), int(nt), _ptr(wt), _ptr(misfit),
+                                         _stream(stream)))
     return misfit

@@ -26,13 +26,14 @@ from . import fwi as F
 
 
 class Inversion:
-    def __init__(self, w, pz, data, shape=None, arena_bytes=1 << 30):
+    def __init__(self, w, pz, data, shape=None, arena_bytes=1 << 30, weights=None):
         self.w, self.pz, self.shape = w, pz, shape
         self.grid = F.make_grid(**w.grid_kwargs())
         d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         self.src, self.rec, self.wav = d(w.src_xy), d(w.rec_xy), d(w.wavelet)
         self.data = F._dev(data)
         self.g = d(shape) if shape is not None else None
+        self.weights = d(weights) if weights is not None else None   # [ns][nr] trace weights
         self.work = F.workspace(self.grid, w.ns, w.nr, F.OP_GRADIENT)
         self.engine = E.Engine(arena_bytes)
         self.alpha = None
@@ -45,7 +46,8 @@ class Inversion:
 
     def gradient(self, m):
         xa, xb = self.fields(m)
-        J, G = F.fwi_gradient(self.grid, self.pz, xa, xb, self.src, self.wav, self.rec, self.data, work=self.work)
+        J, G = F.fwi_gradient(self.grid, self.pz, xa, xb, self.src, self.wav, self.rec, self.data, work=self.work,
+                              weights=self.weights)
         ga, gb = G[self.pz, 0], G[self.pz, 1]
         if self.g is not None:
             g64 = self.g.double()
@@ -65,7 +67,8 @@ class Inversion:
         flat = self.data.reshape(-1)
         while tick:
             for r in self.engine.run(64):
-                F.fwi_misfit(r.traces.reshape(-1), flat, misfit=out[tick.pop(r.ticket)], stream=self.engine.stream)
+                F.fwi_misfit(r.traces.reshape(-1), flat, misfit=out[tick.pop(r.ticket)], stream=self.engine.stream,
+                             weights=self.weights, nt=self.w.nt)
         torch.cuda.synchronize()
         return out.cpu().numpy()
 

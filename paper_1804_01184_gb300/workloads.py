@@ -312,6 +312,9 @@ def bench_bowls(args, Clocks):
     w, g = B.scatterer(args.case)
     shape, which = B.CASES[args.case]
     amp = 0.2
+    ranges = {"all": None, "short": (0.0, 90.0), "long": (135.0, 180.0)}[args.aperture]
+    weights = None if ranges is None else B.aperture_weights(w.src_xy, w.rec_xy, I.centre_of(w.nx, w.nz, w.dx),
+                                                             *ranges)
     data = F.fwi_model(grid_of(w), I.PZ_VP_RHO, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
     dvp, drho = (amp, 0.0) if which == "vp" else (0.0, amp)
     grids = {}
@@ -324,7 +327,7 @@ def bench_bowls(args, Clocks):
     t0 = time.perf_counter()
     shapes, launches = {}, 0
     for pz in range(5):
-        J, l = B.error_bowl(w, g, pz, data, *grids[pz])
+        J, l = B.error_bowl(w, g, pz, data, *grids[pz], weights=weights)
         launches += l
         shapes[["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"][pz]] = {
             k: (round(v, 4) if isinstance(v, float) else [round(x, 4) for x in v]) for k, v in B.bowl_shape(J, *grids[pz]).items()}
@@ -336,7 +339,9 @@ def bench_bowls(args, Clocks):
         "metric": METRIC, "value": round(upd / wall / 1e9, 3), "unit": "Gcell-updates/s", "n_gpus": 1, "steps": 1,
         "warmup": 1, "ms_per_step": round(1e3 * wall, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"bowls-scatterer-{args.case}", "scatterer": f"{shape}, {which} only, contrast {amp}",
+        "config": {"workload": f"bowls-scatterer-{args.case}-aperture-{args.aperture}",
+                   "scatterer": f"{shape}, {which} only, contrast {amp}",
+                   "scattering_angles": "all" if ranges is None else f"{ranges[0]:g}-{ranges[1]:g} degrees",
                    "grid": "121x121 + 40-cell sponge, dx 10 m, 8th order, 1400 steps, 10 shots, 100 receivers, 5 Hz",
                    "bowl": f"{args.bowl_n}x{args.bowl_n} contrasts per parameterization, 5 parameterizations"},
         "solves_per_s": round(solves / wall, 2), "bowls": shapes, "gpu_launches": launches, "clocks": clk,

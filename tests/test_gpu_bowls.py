@@ -54,3 +54,31 @@ def test_bowl_zero_at_truth_and_oracle_values(L, pz):
         assert abs(J[ia, ib] - J_ref) <= r * eb + 0.5 * eb * eb, (ia, ib, J[ia, ib], J_ref)
     s = B.bowl_shape(J, ga, gb, half=1)
     assert s["argmin"] == (float(ga[ta]), float(gb[tb])) and s["condition"] >= 1.0
+
+
+def test_weighted_gradient_is_the_adjoint_of_the_masked_residual(L):
+    """fwi_gradient_weighted with 0/1 aperture weights equals fwi_adjoint given the masked
+    residual w (d_mod - data) bitwise, its misfit equals the masked sum, and all-one weights
+    reproduce fwi_gradient bitwise."""
+    F, B = L
+    w = I.small_case(seed=33, nx=48, nz=44, nt=140, order=8, sponge=6, ns=3, nr=10)
+    c = I.centre_of(w.nx, w.nz, w.dx)
+    w.src_xy, w.rec_xy = I.circle(w.ns, 90.0, c), I.circle(w.nr, 90.0, c, 0.5)
+    g = gpu_grid(w)
+    wt = B.aperture_weights(w.src_xy, w.rec_xy, c, 0.0, 90.0)
+    assert 0 < wt.sum() < wt.size
+    data = I.random_like((w.ns, w.nr, w.nt), 9, 1e3)
+    a0, b0 = w.xi_a * 0.5, w.xi_b * 0.5
+    J, G = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data, weights=wt)
+    tr = F.fwi_model(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy)
+    wd, dd = torch.from_numpy(wt).cuda()[:, :, None], torch.from_numpy(data).cuda()
+    res = (tr - dd) * wd
+    G2 = F.fwi_adjoint(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, res)
+    assert torch.equal(G, G2)
+    r64 = (tr.double() - dd.double()) ** 2 * wd.double()
+    assert abs(J.item() - 0.5 * r64.sum().item()) <= 1e-9 * J.item()
+    Jm = F.fwi_misfit(tr, dd, weights=wt, nt=w.nt).item()
+    assert abs(Jm - J.item()) <= 1e-9 * J.item()
+    J1, G1 = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data, weights=np.ones_like(wt))
+    J0, G0 = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
+    assert torch.equal(G1, G0) and J1.item() == J0.item()
