@@ -3,7 +3,8 @@
 Argument marshalling only: every step of the method runs in the library's CUDA kernels.
 PyTorch supplies device memory (inputs, outputs and the scratch workspace) and streams.
 The functions carry the C names: ``fwi_model``, ``fwi_born``, ``fwi_adjoint``,
-``fwi_gradient``, ``fwi_workspace_bytes``, ``fwi_status``.
+``fwi_gradient`` (optionally weighted per trace), ``fwi_misfit``, ``fwi_workspace_bytes``,
+``fwi_status``, ``fwi_model_noalloc``, ``fwi_set_tile``, ``fwi_set_checkpoint``.
 
 There is no fallback: if libfwi.so has not been built (``paper_1804_01184_gb300.build``)
 or no CUDA device is present, these functions raise.
