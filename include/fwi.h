@@ -197,7 +197,8 @@ int fwi_set_checkpoint(int every);
  * launching stream without blocking, and the shape then keeps its fastest height (launches
  * under stream capture are not timed).  tz > 0 (a multiple of 8) fixes the height instead,
  * for plans made afterwards by any thread (0 restores tuning); variant picks the register
- * budget per thread of the single-job kernels (0 = unbounded, 1 = 128, 2 = 170).  Results are
+ * budget per thread of the single-job kernels (0 = default: unbounded, 170 for the forward
+ * kernel; 1 = 128; 2 = 170).  Results are
  * bitwise identical for every setting; only speed changes. */
 int fwi_set_tile(int tz, int variant);
 

@@ -255,8 +255,10 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         cp_commit();
     };
     float4 vq[R];   // vz rows r-2M+1 .. r (oldest first), shifted every row
+    float4 pq[R];   // this lane's own p float4 of rows g-2M+1 .. g (oldest first): the z-stencil
+                    // reads registers instead of 2M shared rows
 #pragma unroll
-    for (int k = 0; k < R; ++k) vq[k] = f4(0.f);
+    for (int k = 0; k < R; ++k) vq[k] = pq[k] = f4(0.f);
 #pragma unroll
     for (int g = 0; g < FWD_WPD; ++g) issue(g, g, g);
     RingPos<NP> P;      // ring position of row g
@@ -273,10 +275,13 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         const float az = sh.scl[S(0)][0], azh = sh.scl[S(0)][1];
         // vz at half node r + 1/2, r = f - M: p rows r-M+1 .. r+M = rows g-2M+1 .. g
         const int r = f - M;
-        float4 gz = f4(0.f);          // -dt D+z p
+#pragma unroll
+        for (int q = 0; q < R - 1; ++q) pq[q] = pq[q + 1];
+        pq[R - 1] = ld4(ring[P(0)] + L.mo);
+        float4 gz = f4(0.f);          // -dt D+z p (pq[q] is row g - 2M + 1 + q)
 #pragma unroll
         for (int k = 1; k <= M; ++k)
-            gz = ptap(st.nc[k - 1], ld4(ring[P(k - M)] + L.mo), ld4(ring[P(1 - M - k)] + L.mo), gz);
+            gz = ptap(st.nc[k - 1], pq[M - 1 + k], pq[M - k], gz);
         const float4 vz = pmul(pmul(azh, axv), pfma(ld4(sg[1] + L.mo), gz, ld4(sg[0] + L.mo)));
         if (L.wr && r >= z0 && r < zend) st4(VZ1 + r * d.Px + L.mc, vz);
 #pragma unroll
@@ -298,7 +303,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
             for (int k = 1; k <= M; ++k)   // vq[q] is vz row j - M + q
                 dv = ptap(st.nc[k - 1], vq[M + k - 1], vq[M - k], dv);
             const float4 Kv = ld4(sg[4] + L.mo);
-            float4 pn = pmul(pmul(az, axv), pfma(Kv, dv, ld4(prow + L.mo)));
+            float4 pn = pmul(pmul(az, axv), pfma(Kv, dv, pq[0]));
             if (hsrc) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
@@ -502,8 +507,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
     // qq: K d_p pbar rows f-2M+1 .. f (z-stencil of u_z); bq: bz u_z rows r-2M+1 .. r (z-stencil of
     // pbar); oldest first, shifted every row
     float4 qq[R], bq[R];
+    float4 pq[R];   // this lane's own p^n float4 of rows g-2M+1 .. g (z-stencil from registers)
 #pragma unroll
-    for (int k = 0; k < R; ++k) { qq[k] = f4(0.f); bq[k] = f4(0.f); }
+    for (int k = 0; k < R; ++k) { qq[k] = f4(0.f); bq[k] = f4(0.f); pq[k] = f4(0.f); }
 #pragma unroll
     for (int g = 0; g < ADJ_WPD; ++g) issue(g, g, g);
     RingPos<NP> P;      // ring position of row g in pr
@@ -529,11 +535,14 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
         if (!L.own) st4(qrow + L.eo, pmul(pmul(azf, axe), pmul(ld4(sg[1] + L.eo), ld4(sg[0] + L.eo))));
         // u_z at half node r + 1/2, r = f - M
         const int r = f - M;
+#pragma unroll
+        for (int q = 0; q < R - 1; ++q) pq[q] = pq[q + 1];
+        pq[R - 1] = ld4(pr[P(0)] + L.mo);
         float4 gq = f4(0.f), gp = f4(0.f);
 #pragma unroll
-        for (int k = 1; k <= M; ++k) {   // qq[q] is row f - 2M + 1 + q = r - M + 1 + q
+        for (int k = 1; k <= M; ++k) {   // qq[q], pq[q] are row f - 2M + 1 + q = r - M + 1 + q
             gq = ptap(st.c[k - 1], qq[M - 1 + k], qq[M - k], gq);
-            gp = ptap(st.c[k - 1], ld4(pr[P(k - M)] + L.mo), ld4(pr[P(1 - M - k)] + L.mo), gp);
+            gp = ptap(st.c[k - 1], pq[M - 1 + k], pq[M - k], gp);
         }
         const float4 uz = pmul(pmul(azh, axv), padd(ld4(sg[2] + L.mo), gq));
 #pragma unroll
@@ -563,7 +572,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
             const float4 dp = pmul(az, axv);
             st4(A1 + j * d.Px + L.mc, pfma(dp, ld4(sg[6] + L.mo), dv));
             // pbar^n - d_p pbar^{n+1} is exactly the divergence term dv
-            red_add4(GK + j * d.Px + L.mc, pmul(ld4(pj + L.mo), dv));
+            red_add4(GK + j * d.Px + L.mc, pmul(pq[0], dv));
         }
         P.next();
         S.next();
@@ -714,8 +723,9 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         cp_commit();
     };
     float4 vq[R], uq[R];   // vz and uz rows r-2M+1 .. r, oldest first
+    float4 pq[R];          // this lane's own p float4 of rows g-2M+1 .. g (z-stencil from registers)
 #pragma unroll
-    for (int k = 0; k < R; ++k) { vq[k] = f4(0.f); uq[k] = f4(0.f); }
+    for (int k = 0; k < R; ++k) { vq[k] = f4(0.f); uq[k] = f4(0.f); pq[k] = f4(0.f); }
 #pragma unroll
     for (int g = 0; g < BORN_WPD; ++g) issue(g, g, g);
     RingPos<NP> P;      // ring position of row g
@@ -731,11 +741,14 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         float(*sg)[WROW] = stg[S(0)];
         const float az = sh.scl[S(0)][0], azh = sh.scl[S(0)][1];
         const int r = f - M;
-        float4 gp = f4(0.f), gq = f4(0.f);     // -dt D+z p, -dt D+z q
+#pragma unroll
+        for (int q = 0; q < R - 1; ++q) pq[q] = pq[q + 1];
+        pq[R - 1] = ld4(spr[P(0)] + L.mo);
+        float4 gp = f4(0.f), gq = f4(0.f);     // -dt D+z p, -dt D+z q (pq[q] is row g - 2M + 1 + q)
 #pragma unroll
         for (int k = 1; k <= M; ++k) {
             const int a = P(k - M), b = P(1 - M - k);
-            gp = ptap(st.nc[k - 1], ld4(spr[a] + L.mo), ld4(spr[b] + L.mo), gp);
+            gp = ptap(st.nc[k - 1], pq[M - 1 + k], pq[M - k], gp);
             gq = ptap(st.nc[k - 1], ld4(sqr[a] + L.mo), ld4(sqr[b] + L.mo), gq);
         }
         const float4 fz = pmul(azh, axv), bz = ld4(sg[2] + L.mo);
@@ -773,7 +786,7 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
                 du = ptap(st.nc[k - 1], uq[M + k - 1], uq[M - k], du);
             }
             const float4 K = ld4(sg[8] + L.mo), dK = ld4(sg[9] + L.mo), fp = pmul(az, axv);
-            float4 pn = pmul(fp, pfma(K, dv, ld4(prow + L.mo)));
+            float4 pn = pmul(fp, pfma(K, dv, pq[0]));
             float4 qn = pmul(fp, pfma(dK, dv, pfma(K, du, ld4(qrow + L.mo))));
             if (hsrc) {
 #pragma unroll
