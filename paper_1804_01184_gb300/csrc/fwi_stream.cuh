@@ -80,11 +80,13 @@ __device__ __forceinline__ float4 mask4(float4 v, int c0, int Nx)
 
 // D+ along x of a shared row at the four half nodes c0+1/2 .. c0+3+1/2 (c0 = 4*tid):
 // sum_k c_k (f[i+k] - f[i-k+1]) needs columns c0-3 .. c0+7 = three aligned float4.
+// b: the row's float4 at c0 when the caller already holds it in registers (one shared load
+// fewer), else read here.
 template <int M>
-__device__ __forceinline__ float4 row_dplus(const float *row, int c0, const float *cf)
+__device__ __forceinline__ float4 row_dplus(const float *row, int c0, const float4 &b, const float *cf)
 {
     float w[12];
-    const float4 a = ld4(row + c0 - 4), b = ld4(row + c0), c = ld4(row + c0 + 4);
+    const float4 a = ld4(row + c0 - 4), c = ld4(row + c0 + 4);
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
     w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
     float o[4];
@@ -98,13 +100,19 @@ __device__ __forceinline__ float4 row_dplus(const float *row, int c0, const floa
     return make_float4(o[0], o[1], o[2], o[3]);
 }
 
+template <int M>
+__device__ __forceinline__ float4 row_dplus(const float *row, int c0, const float *cf)
+{
+    return row_dplus<M>(row, c0, ld4(row + c0), cf);
+}
+
 // D- along x of a shared half-node row at the four nodes c0 .. c0+3:
 // sum_k c_k (g[i+k-1] - g[i-k]) needs columns c0-4 .. c0+6.
 template <int M>
-__device__ __forceinline__ float4 row_dminus(const float *row, int c0, const float *cf)
+__device__ __forceinline__ float4 row_dminus(const float *row, int c0, const float4 &b, const float *cf)
 {
     float w[12];
-    const float4 a = ld4(row + c0 - 4), b = ld4(row + c0), c = ld4(row + c0 + 4);
+    const float4 a = ld4(row + c0 - 4), c = ld4(row + c0 + 4);
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
     w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
     float o[4];
@@ -116,6 +124,12 @@ __device__ __forceinline__ float4 row_dminus(const float *row, int c0, const flo
         o[q] = g;
     }
     return make_float4(o[0], o[1], o[2], o[3]);
+}
+
+template <int M>
+__device__ __forceinline__ float4 row_dminus(const float *row, int c0, const float *cf)
+{
+    return row_dminus<M>(row, c0, ld4(row + c0), cf);
 }
 
 // Shared layout of one row: SHALO zeros, 4*NT columns, SHALO zeros.

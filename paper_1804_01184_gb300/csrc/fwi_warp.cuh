@@ -291,14 +291,14 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         const int j = f - R + 1;
         const bool row = j >= z0 && j < zend;
         const float *prow = ring[P(1 - R)];
-        const float4 gx = row_dplus<M>(prow, L.mo, st.nc);        // -dt D+x p
+        const float4 gx = row_dplus<M>(prow, L.mo, pq[0], st.nc);        // -dt D+x p
         const float4 vx = pmul(pmul(az, axhv), pfma(ld4(sg[3] + L.mo), gx, ld4(sg[2] + L.mo)));
         float *vrow = vxr[f & 1];
         st4(vrow + L.mo, vx);
         if (row && L.wr) st4(VX1 + j * d.Px + L.mc, vx);
         __syncwarp();
         if (row && L.wr) {
-            float4 dv = row_dminus<M>(vrow, L.mo, st.nc);          // -dt D-x vx
+            float4 dv = row_dminus<M>(vrow, L.mo, vx, st.nc);          // -dt D-x vx
 #pragma unroll
             for (int k = 1; k <= M; ++k)   // vq[q] is vz row j - M + q
                 dv = ptap(st.nc[k - 1], vq[M + k - 1], vq[M - k], dv);
@@ -556,16 +556,17 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
         const int j = f - R + 1;
         const bool row = j >= z0 && j < zend;
         const float *pj = pr[P(1 - R)];
-        const float4 ux = pmul(pmul(az, axhv), padd(ld4(sg[4] + L.mo), row_dplus<M>(qr[Q(1 - R)], L.mo, st.c)));
+        const float4 ux = pmul(pmul(az, axhv), padd(ld4(sg[4] + L.mo), row_dplus<M>(qr[Q(1 - R)], L.mo, qq[0], st.c)));
         float *brow = bur[f & 1];
-        st4(brow + L.mo, pmul(ld4(sg[5] + L.mo), ux));
+        const float4 bux = pmul(ld4(sg[5] + L.mo), ux);
+        st4(brow + L.mo, bux);
         if (row && L.wr) {
             st4(AX1 + j * d.Px + L.mc, ux);
-            red_add4(GX + j * d.Px + L.mc, pmul(ux, row_dplus<M>(pj, L.mo, st.c)));
+            red_add4(GX + j * d.Px + L.mc, pmul(ux, row_dplus<M>(pj, L.mo, pq[0], st.c)));
         }
         __syncwarp();
         if (row && L.wr) {
-            float4 dv = row_dminus<M>(brow, L.mo, st.c);
+            float4 dv = row_dminus<M>(brow, L.mo, bux, st.c);
 #pragma unroll
             for (int k = 1; k <= M; ++k)   // bq[q] is row j - M + q
                 dv = ptap(st.c[k - 1], bq[M + k - 1], bq[M - k], dv);
@@ -767,7 +768,7 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         const int sj = P(1 - R);
         const float *prow = spr[sj], *qrow = sqr[sj];
         const float4 fx = pmul(az, axhv), bx = ld4(sg[6] + L.mo);
-        const float4 gpx = row_dplus<M>(prow, L.mo, st.nc);
+        const float4 gpx = row_dplus<M>(prow, L.mo, pq[0], st.nc);
         const float4 vx = pmul(fx, pfma(bx, gpx, ld4(sg[4] + L.mo)));
         const float4 ux = pmul(fx, pfma(ld4(sg[7] + L.mo), gpx, pfma(bx, row_dplus<M>(qrow, L.mo, st.nc), ld4(sg[5] + L.mo))));
         float *vrow = svr[f & 1], *urow = sur[f & 1];
@@ -779,7 +780,7 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         }
         __syncwarp();
         if (row && L.wr) {
-            float4 dv = row_dminus<M>(vrow, L.mo, st.nc), du = row_dminus<M>(urow, L.mo, st.nc);
+            float4 dv = row_dminus<M>(vrow, L.mo, vx, st.nc), du = row_dminus<M>(urow, L.mo, ux, st.nc);
 #pragma unroll
             for (int k = 1; k <= M; ++k) {   // vq[q] is vz row j - M + q
                 dv = ptap(st.nc[k - 1], vq[M + k - 1], vq[M - k], dv);
