@@ -195,7 +195,7 @@ int fwi_set_checkpoint(int every);
  * the first launches try the height an occupancy rule picks (strips that just fill the warps
  * the GPU holds at once) and a few others, each timed twice with CUDA events on the
  * launching stream without blocking, and the shape then keeps its fastest height (launches
- * under stream capture are not timed).  tz > 0 (a multiple of 8) fixes the height instead,
+ * under stream capture are not timed).  tz > 0 (any number of rows) fixes the height instead,
  * for plans made afterwards by any thread (0 restores tuning); variant picks the register
  * budget per thread of the single-job kernels (0 = default: unbounded, 170 for the forward
  * kernel; 1 = 128; 2 = 170).  Results are

@@ -366,11 +366,16 @@ int strip_height_for_rows(long long rows, int resident)
 
 // Online strip-height tuner (the measured half of the autotuner).  For each launch shape --
 // (kernel, grid, shots) for the single-job calls, (kernel, quarter-octave bucket of the total
-// strip rows) for the engine's batched launches -- the first launches try candidate heights
-// (the rule's height and 32 .. 120), each twice, timed by an event pair on the launching
-// stream.  The timings are collected without blocking as later launches of the same shape
-// arrive; once every candidate has two, the shape keeps its fastest height.  Launches under
-// stream capture are not timed and use the rule's height (or the shape's chosen one).
+// strip rows) for the engine's batched launches -- the first launches try candidate heights,
+// each twice, timed by an event pair on the launching stream.  A single-job shape tries the
+// rule's height and the heights that cut its Nz rows into c equal strips, ceil(Nz / c), for
+// every c from ceil(Nz / 136) to ceil(Nz / 32) (heights with equal strip counts differ only in
+// the last strip, and the even split is the one worth timing; measured on 681 rows, the best
+// height moved between 60 and 124 with the kernel and the shot count); a batched shape, whose
+// jobs have different heights, tries the rule's height and 32 .. 120.  The timings are
+// collected without blocking as later launches of the same shape arrive; once every candidate
+// has two, the shape keeps its fastest height.  Launches under stream capture are not timed
+// and use the rule's height (or the shape's chosen one).
 class StripTuner {
 public:
     struct Slot {
@@ -383,7 +388,8 @@ public:
 
     // Height for the next launch of shape `key` on `st`; when the launch is to be timed the
     // start event is already recorded and finish(slot) must follow the launch.
-    Slot pick(const Key &key, int rule, cudaStream_t st)
+    // nz > 0: the launch covers one grid of nz rows (even-split candidates)
+    Slot pick(const Key &key, int rule, cudaStream_t st, int nz = 0)
     {
         Slot s;
         s.tz = rule;
@@ -394,7 +400,7 @@ public:
         }
         std::lock_guard<std::mutex> lk(mu_);
         Shape &sh = shapes_[key];
-        if (sh.cand.empty()) init(sh, rule);
+        if (sh.cand.empty()) init(sh, rule, nz);
         poll(sh);
         if (sh.chosen) {
             s.tz = sh.chosen;
@@ -447,9 +453,14 @@ private:
         int chosen = 0;
     };
 
-    void init(Shape &sh, int rule)
+    void init(Shape &sh, int rule, int nz)
     {
-        std::set<int> c = {rule, 32, 40, 48, 56, 64, 80, 96, 120};
+        std::set<int> c = {rule};
+        if (nz > 0) {
+            for (int k = (nz + 135) / 136; k <= (nz + 31) / 32; ++k) c.insert((nz + k - 1) / k);
+        } else {
+            c.insert({32, 40, 48, 56, 64, 80, 96, 120});
+        }
         sh.cand.assign(c.begin(), c.end());
         sh.nsamp.assign(sh.cand.size(), 0);
         sh.inflight.assign(sh.cand.size(), 0);
@@ -525,7 +536,7 @@ StripTuner::Slot tuned_height(int fixed, const void *kernel, const fwi::Dims &d,
     s.tz = strip_height(fixed, d, shots, resident);
     if (fixed > 0) return s;
     key = StripTuner::Key{kernel, ((long long)d.Nx << 32) | (unsigned)d.Nz, shots, 0};
-    return g_tuner.pick(key, s.tz, st);
+    return g_tuner.pick(key, s.tz, st, d.Nz);
 }
 
 // Warp-strip launch shape: one warp per (120-column strip, tz-row strip, shot), then
@@ -953,8 +964,8 @@ int fwi_set_checkpoint(int every)
 
 int fwi_set_tile(int tz, int variant)
 {
-    if (tz < 0 || tz % 8 || variant < 0 || variant > 2)
-        return fail(FWI_EINVAL, "tile height must be a multiple of 8, variant 0, 1 or 2");
+    if (tz < 0 || variant < 0 || variant > 2)
+        return fail(FWI_EINVAL, "tile height must be >= 0, variant 0, 1 or 2");
     g_tile_tz = tz;
     g_tile_variant = variant;
     return FWI_OK;

@@ -294,7 +294,7 @@ def test_strip_heights_give_bitwise_identical_results(F):
     data = I.random_like((w.ns, w.nr, w.nt), 5, 1e3)
     out = []
     try:
-        for tz in (0, 8, 16, 24, 64, 200):
+        for tz in (0, 8, 13, 16, 24, 36, 64, 200):
             F.fwi_set_tile(tz, 0)
             tr = run_model(F, w)
             bo = F.fwi_born(g, w.pz, w.xi_a, w.xi_b, da, db, w.src_xy, w.wavelet, w.rec_xy).cpu().numpy()
