@@ -29,6 +29,12 @@ experiments, Sec. "Almost Well-posed Example" and the scatterer table):
     probability 1/2) with contrasts drawn uniformly from [-0.5, 0.5] in vp and in rho.
   * ``poisson_arrivals`` -- seeded Poisson request times.
   * ``small_case`` -- seeded random heterogeneous models on small grids for parity tests.
+  * ``freq_paper`` -- the frequency-domain Born workload of Schemes I/II: the paper's
+    acquisition (10 sources, 100 receivers on a 490 m circle around x_0 = (0, 0), vp 2000 m/s,
+    rho 2000 kg/m^3), a 121 x 121 model grid at dx 5 m centred on x_0 (inside the circle),
+    the 5 Hz Ricker's spectrum at f_k = k 0.25 Hz, k = 1 .. 60, and a point or Gaussian
+    (sigma 50 m) scatterer in vp or rho.
+  * ``small_freq_case`` -- seeded random frequency-domain cases on small grids.
 """
 from __future__ import annotations
 
@@ -250,3 +256,98 @@ def small_case(seed=0, nx=45, nz=37, nt=120, order=8, sponge=6, ns=3, nr=7, pz=P
 def random_like(shape, seed, scale=1.0):
     """Seeded standard-normal float32 array (perturbations, residuals, test vectors)."""
     return (np.random.default_rng(seed).standard_normal(shape) * scale).astype(np.float32)
+
+
+# ---------------------------------------------------------------- frequency-domain inputs
+
+def ricker_spectrum(freqs, f_peak, t0=None):
+    """Spectrum S(f) = integral w(t) e^{+i 2 pi f t} dt of the Ricker wavelet of peak f_peak
+    delayed by t0 (default 1/f_peak), amplitude 1 (the e^{-i w t} convention):
+    (2 / sqrt(pi)) (f^2 / f_peak^3) exp(-f^2 / f_peak^2) e^{i 2 pi f t0}; complex128."""
+    t0 = 1.0 / f_peak if t0 is None else t0
+    f = np.asarray(freqs, np.float64)
+    amp = 2.0 / math.sqrt(math.pi) * f * f / f_peak ** 3 * np.exp(-(f / f_peak) ** 2)
+    return amp * np.exp(2j * math.pi * f * t0)
+
+
+@dataclasses.dataclass
+class FreqWorkload:
+    name: str
+    nx: int
+    nz: int
+    dx: float
+    x0: float               # coordinates of model node (0, 0)
+    z0: float
+    vp_o: float
+    rho_o: float
+    pz: int
+    xi_a: np.ndarray        # [nz][nx] float32 contrasts of parameterization pz
+    xi_b: np.ndarray
+    src_xy: np.ndarray      # [ns][2] float32 metres
+    rec_xy: np.ndarray      # [nr][2] float32
+    freqs: np.ndarray       # [nf] float64 Hz
+    spectrum: np.ndarray    # [nf] complex64 S(w_k)
+
+    @property
+    def ns(self):
+        return self.src_xy.shape[0]
+
+    @property
+    def nr(self):
+        return self.rec_xy.shape[0]
+
+    @property
+    def nf(self):
+        return self.freqs.shape[0]
+
+    def fgrid_kwargs(self):
+        return dict(nx=self.nx, nz=self.nz, dx=self.dx, x0=self.x0, z0=self.z0, vp_o=self.vp_o,
+                    rho_o=self.rho_o)
+
+    def terms(self):
+        """(frequency, source, receiver, node) terms of one pass over the data."""
+        return self.nf * self.ns * self.nr * self.nx * self.nz
+
+    def centre_index(self):
+        return (self.nz // 2) * self.nx + self.nx // 2
+
+
+def freq_paper(n=121, dx=5.0, which="vp", amplitude=0.2, shape="gaussian", nf=60, df=0.25,
+               pz=PZ_VP_RHO, f_peak=5.0, ns=10, nr=100, radius=490.0):
+    """The paper's almost well-posed example for the frequency-domain schemes; x_0 = (0, 0)
+    is the centre node.  The contrasts are in vp-rho (parameterization A) unless pz says
+    otherwise (the scatterer is then given in vp-rho and not converted: callers pass pz=0)."""
+    h = (n - 1) / 2.0 * dx
+    g = point(n, n) if shape == "point" else gaussian(n, n, dx, (h, h), 50.0)
+    g = g * np.float32(amplitude)
+    z = np.zeros_like(g)
+    xa, xb = (g, z) if which == "vp" else (z, g)
+    freqs = df * np.arange(1, nf + 1, dtype=np.float64)
+    return FreqWorkload(f"freq-paper-{n}x{n}-{shape}-{which}", n, n, dx, -h, -h, 2000.0, 2000.0, pz, xa, xb,
+                        circle(ns, radius, (0.0, 0.0)), circle(nr, radius, (0.0, 0.0), 0.5), freqs,
+                        ricker_spectrum(freqs, f_peak).astype(np.complex64))
+
+
+def small_freq_case(seed=0, nx=23, nz=19, dx=5.0, ns=3, nr=7, nf=5, amp=0.15, pz=PZ_VP_RHO,
+                    radius=200.0, f_peak=8.0):
+    """Seeded small frequency-domain case: smooth random contrasts of size ~amp on a grid
+    centred at (0, 0), sources and receivers at random angles on a circle outside the grid,
+    random frequencies in (0.5 f_peak, 2.5 f_peak)."""
+    rng = np.random.default_rng(seed)
+
+    def smooth():
+        f = rng.standard_normal((nz, nx))
+        for _ in range(2):
+            f = (np.roll(f, 1, 0) + f + np.roll(f, -1, 0)) / 3.0
+            f = (np.roll(f, 1, 1) + f + np.roll(f, -1, 1)) / 3.0
+        f /= max(1e-12, np.abs(f).max())
+        return (amp * f).astype(np.float32)
+
+    def ring(k):
+        th = 2.0 * math.pi * rng.random(k)
+        return np.stack([radius * np.cos(th), radius * np.sin(th)], axis=1).astype(np.float32)
+
+    freqs = np.sort(f_peak * (0.5 + 2.0 * rng.random(nf)))
+    return FreqWorkload(f"small-freq-{nx}x{nz}-s{seed}", nx, nz, dx, -(nx - 1) / 2.0 * dx, -(nz - 1) / 2.0 * dx,
+                        2000.0, 2000.0, pz, smooth(), smooth(), ring(ns), ring(nr), freqs,
+                        ricker_spectrum(freqs, f_peak).astype(np.complex64))
