@@ -32,6 +32,9 @@ Two more workloads run through the batching engine (one JSON line each, 1 GPU):
   --workload differentiation : one FWI gradient through torch.autograd on the 1201 x 1201,
                      6000-step, 16-shot smooth-background workload with checkpoints every 200
                      steps (per step: forward, torch misfit, backward).
+  --workload fborn : the frequency-domain Born path of Schemes I/II on the paper's acquisition
+                     (per step, for each parameterization: a Scheme I gradient and the Hessian
+                     column at x_0); Born W-terms per second.
 """
 from __future__ import annotations
 
@@ -103,7 +106,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="gradient workspace budget (0: 80%% of free device memory)")
     ap.add_argument("--workload", default="gaussian",
-                    choices=["gaussian", "batch", "serve", "differentiation", "bowls", "invert"])
+                    choices=["gaussian", "batch", "serve", "differentiation", "bowls", "invert", "fborn"])
     ap.add_argument("--iters", type=int, default=15, help="invert: iterations")
     ap.add_argument("--case", default="ii", choices=["i", "ii", "iv", "v"], help="bowls: scatterer")
     ap.add_argument("--bowl-n", type=int, default=21, help="bowls: contrasts per axis")
@@ -199,6 +202,24 @@ def cpu_sample(nt_sample=300, shots=(0,)):
     cells = w.Nx * w.Nz * w.nt * w.ns * 4
     return cells / dt / 1e9, dt, cells
 
+def fborn_cpu_sample(w, nf=2):
+    """The FP64 oracle's Scheme I gradient on the first nf frequencies of the workload (full
+    grid and acquisition), scaled to W-terms per second (two passes)."""
+    import numpy as np
+
+    import oracle.fborn as OF
+    fg = OF.FGrid(**w.fgrid_kwargs())
+    fr, sp = w.freqs[:nf], w.spectrum[:nf]
+    q = OF.model(fg, fr, sp, w.src_xy, w.rec_xy, 0, w.xi_a, w.xi_b, OF.NONLINEAR)
+    a0 = np.zeros_like(w.xi_a, dtype=np.float64)
+    t0 = time.perf_counter()
+    OF.gradient(fg, fr, sp, w.src_xy, w.rec_xy, 0, a0, a0, q, OF.LINEAR)
+    dt = time.perf_counter() - t0
+    terms = nf * w.ns * w.nr * w.nx * w.nz
+    return {"value": round(2 * terms / dt / 1e9, 4), "unit": "GW-terms/s", "cores": 1,
+            "kind": "oracle", "sample": f"Scheme I gradient (vp-rho), {nf} of {w.nf} frequencies, full grid and "
+                                        f"acquisition (numpy FP64, one thread, {dt:.1f} s)"}
+
 
 def run_reference(args, rank):
     if rank != 0:
@@ -237,7 +258,8 @@ def main():
         from paper_1804_01184_gb300 import workloads
         {"batch": workloads.bench_batch, "serve": workloads.bench_serve,
          "differentiation": workloads.bench_differentiation, "bowls": workloads.bench_bowls,
-         "invert": workloads.bench_invert}[args.workload](args, Clocks)
+         "invert": workloads.bench_invert,
+         "fborn": lambda a, c: workloads.bench_fborn(a, c, fborn_cpu_sample)}[args.workload](args, Clocks)
         return
     import numpy as np
     import torch

@@ -277,6 +277,75 @@ int fwi_engine_destroy(fwi_engine *engine);
 int fwi_profile(int enable);
 int fwi_profile_report(char *buf, size_t len);
 
+/* ---------------------------------------------------------------------------------------
+ * Frequency-domain Born modelling of Schemes I and II (Sec. "Modelling and Inversion",
+ * eqn:param_born and eqn:param_pfreq1; Sec. "Point-scatterer Analysis", eqn:param_Hker).
+ *
+ * The reference medium is homogeneous (vp_o, rho_o, K_o = rho_o vp_o^2).  Its Green function
+ * is G_o(x; p) = (i rho_o / 4) H_0^(1)(k |x - p|), k = 2 pi f / vp_o (e^{-i w t} convention;
+ * the sign that makes the printed Lippmann-Schwinger equation exact; misfits, gradients and
+ * Hessians do not depend on it).  The modelling vector of node x for source s and receiver r
+ * is W = [w^2/K_o G_o(x; r) G_o(x; s),  -(1/rho_o) grad G_o(x; r) . grad G_o(x; s)], and the
+ * Born data are
+ *     p[f][s][r] = S_f ( G_o(x_r; x_s) + dx^2 sum_x W(x) . (xi_{1/K}(x), xi_{1/rho}(x)) ),
+ * where (xi_{1/K}, xi_{1/rho}) are the contrasts of parameterization pz mapped LINEARLY
+ * (scheme FWI_FB_LINEAR, Scheme I: the linearization at zero contrast behind Table 3; for the
+ * impedance -(xi_{1/K} + xi_{1/rho})/2) or EXACTLY (FWI_FB_NONLINEAR, Scheme II: Table 2).
+ * The misfit is J = 1/2 sum_{f,s,r} |p - q|^2 over the given frequencies (all w > 0).
+ *
+ * Model grid: nx x nz nodes, x fastest, node (i, j) at (x0 + i dx, z0 + j dx) metres;
+ * sources and receivers are points anywhere at least dx/2 from every node.
+ * Complex arrays are interleaved float pairs (re, im).  Device pointers as elsewhere,
+ * except the host arrays of fwi_fborn_tables. */
+typedef struct {
+    int nx, nz;          /* model nodes */
+    int nf;              /* frequencies */
+    double dx;           /* node spacing (m) */
+    double x0, z0;       /* coordinates of node (0, 0) (m) */
+    double vp_o, rho_o;  /* homogeneous reference medium (m/s, kg/m^3) */
+} fwi_fgrid;
+
+#define FWI_FB_LINEAR    1   /* Scheme I map  */
+#define FWI_FB_NONLINEAR 2   /* Scheme II map */
+
+/* Bytes of the workspace of a geometry of ns sources and nr receivers on grid g (0 if the
+ * sizes are invalid): Green tables G_o and dG_o/dr for every (frequency, point, node) --
+ * 16 nf (ns + nr) nx nz bytes -- plus per-call scratch. */
+size_t fwi_fborn_workspace_bytes(const fwi_fgrid *g, int ns, int nr);
+
+/* Fills the workspace for one acquisition: freqs [nf] (Hz, > 0), spectrum [nf] complex
+ * S(w_f), src_xy [ns][2], rec_xy [nr][2] -- HOST arrays, copied before the call returns --
+ * and the Green tables of every source and receiver at every node and frequency (double-
+ * precision Bessel functions, stored as float pairs).  FWI_EINVAL for a point within dx/2 of
+ * a node, a non-positive frequency or bad sizes; FWI_ENOMEM if work_bytes is too small.  The
+ * other fwi_fborn_* calls read this workspace with the same (g, ns, nr). */
+int fwi_fborn_tables(const fwi_fgrid *g, const double *freqs, const float *spectrum, const float *src_xy, int ns,
+                     const float *rec_xy, int nr, void *work, size_t work_bytes, void *stream);
+
+/* Born data p [nf][ns][nr] complex (eqn:param_pfreq1) of the contrasts xi_a, xi_b [nz][nx] of
+ * parameterization pz under `scheme`; incident != 0 adds the direct field S_f G_o(x_r; x_s)
+ * (0: the scattered part only).  FWI_EINVAL for bad arguments (a contrast with 1 + xi <= 0 under
+ * the exact map gives non-finite data). */
+int fwi_fborn_model(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param pz, const float *xi_a,
+                    const float *xi_b, int incident, void *work, float *data, void *stream);
+
+/* Misfit J (one double) and its gradient grad [2][nz][nx] (double; dJ/dxi_a then dJ/dxi_b)
+ * at the contrasts xi_a, xi_b of pz under `scheme`, against observed data q [nf][ns][nr]
+ * complex (with the direct field, as fwi_fborn_model(incident = 1) gives it):
+ * dJ/dxi_{1/K,1/rho}(x) = Re sum conj(p - q) S_f W(x) dx^2, then the chain rule through
+ * the map's Jacobian at each node. */
+int fwi_fborn_gradient(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param pz, const float *xi_a,
+                       const float *xi_b, const float *data_obs, void *work, double *misfit, double *grad,
+                       void *stream);
+
+/* Scheme I Hessian terms H [2][2][nz][nx] (double): H[a][b][i] = d^2 J / d xi_a(x_i) d xi_b(x_j)
+ * for the fixed node j = (jx, jz) and every node i -- the real part of
+ * dx^4 sum_f |S_f|^2 sum_{s,r} conj(W_a(x_i)) W_b(x_j) taken through the linear map of pz (the
+ * Gauss-Newton Hessian, exact for Scheme I).  H[.][.][j] is the reduced Hessian of
+ * eqn:param_Hker.  FWI_EINVAL for a node off the grid or more than 2048 sources + receivers. */
+int fwi_fborn_hessian(const fwi_fgrid *g, int ns, int nr, fwi_param pz, int jx, int jz, void *work, double *H,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

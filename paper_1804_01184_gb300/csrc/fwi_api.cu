@@ -787,6 +787,7 @@ void set_error(const char *msg) { g_err = msg ? msg : ""; }
 
 #include "fwi_arena.h"
 #include "fwi_engine.inc"
+#include "fwi_fborn.inc"
 
 extern "C" {
 

@@ -331,8 +331,8 @@ def freq_paper(n=121, dx=5.0, which="vp", amplitude=0.2, shape="gaussian", nf=60
 def small_freq_case(seed=0, nx=23, nz=19, dx=5.0, ns=3, nr=7, nf=5, amp=0.15, pz=PZ_VP_RHO,
                     radius=200.0, f_peak=8.0):
     """Seeded small frequency-domain case: smooth random contrasts of size ~amp on a grid
-    centred at (0, 0), sources and receivers at random angles on a circle outside the grid,
-    random frequencies in (0.5 f_peak, 2.5 f_peak)."""
+    centred at (0, 0), sources at random angles on a circle of `radius` outside the grid and
+    receivers on one of 1.25 radius, random frequencies in (0.5 f_peak, 2.5 f_peak)."""
     rng = np.random.default_rng(seed)
 
     def smooth():
@@ -343,11 +343,11 @@ def small_freq_case(seed=0, nx=23, nz=19, dx=5.0, ns=3, nr=7, nf=5, amp=0.15, pz
         f /= max(1e-12, np.abs(f).max())
         return (amp * f).astype(np.float32)
 
-    def ring(k):
+    def ring(k, rad):
         th = 2.0 * math.pi * rng.random(k)
-        return np.stack([radius * np.cos(th), radius * np.sin(th)], axis=1).astype(np.float32)
+        return np.stack([rad * np.cos(th), rad * np.sin(th)], axis=1).astype(np.float32)
 
     freqs = np.sort(f_peak * (0.5 + 2.0 * rng.random(nf)))
     return FreqWorkload(f"small-freq-{nx}x{nz}-s{seed}", nx, nz, dx, -(nx - 1) / 2.0 * dx, -(nz - 1) / 2.0 * dx,
-                        2000.0, 2000.0, pz, smooth(), smooth(), ring(ns), ring(nr), freqs,
+                        2000.0, 2000.0, pz, smooth(), smooth(), ring(ns, radius), ring(nr, 1.25 * radius), freqs,
                         ricker_spectrum(freqs, f_peak).astype(np.complex64))

@@ -383,3 +383,109 @@ def bench_invert(args, Clocks):
         "inversions": res, "clocks": clk,
     }
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------ frequency-domain Born (I/II)
+
+FB_FLOPS_PER_TERM = 24      # three complex multiply-adds per (frequency, source, receiver, node)
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak of the GPU at the given SM clock: SMs x 128 lanes x 2 flops x clock."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def bench_fborn(args, Clocks, cpu_sample=None):
+    """Frequency-domain Born kernels of Schemes I/II on the paper's acquisition (121 x 121
+    nodes at 5 m around x_0, 10 sources and 100 receivers on the 490 m circle, 60 frequencies
+    0.25 - 15 Hz with the 5 Hz Ricker spectrum; observed data of the Gaussian vp scatterer,
+    contrast 0.2, under the exact map).  One step: for each of the five parameterizations, the
+    Scheme I misfit gradient at a seeded model (data contraction, misfit, gradient contraction)
+    and the Hessian column at x_0 (whose centre is the reduced Hessian).  A term is one
+    (frequency, source, receiver, node) product of W; a gradient takes two passes over them.
+    cpu_sample(w), when given, times the CPU baseline."""
+    from . import fborn as FBN
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = I.freq_paper()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    acq = FBN.acquisition(w)
+    torch.cuda.synchronize()
+    tables_ms = 1e3 * (time.perf_counter() - t0)
+    q = acq.model(I.PZ_VP_RHO, w.xi_a, w.xi_b, scheme=FBN.NONLINEAR)
+    models = [(torch.from_numpy(I.random_like((w.nz, w.nx), 40 + pz, 0.05)).to(dev),
+               torch.from_numpy(I.random_like((w.nz, w.nx), 50 + pz, 0.05)).to(dev)) for pz in range(5)]
+    J = torch.empty((5, 1), dtype=torch.float64, device=dev)
+    G = torch.empty((5, 2, w.nz, w.nx), dtype=torch.float64, device=dev)
+    H = torch.empty((5, 2, 2, w.nz, w.nx), dtype=torch.float64, device=dev)
+    c = w.nx // 2
+
+    def step():
+        for pz in range(5):
+            acq.gradient(pz, *models[pz], q, scheme=FBN.LINEAR, misfit=J[pz], grad=G[pz])
+            acq.hessian(pz, c, c, out=H[pz])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    kernel_profile(True)
+    clocks = Clocks(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = kernel_profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    terms = w.terms()
+    passes = 2 * 5
+    # end to end through the public API: host contrasts and observed data in, misfit, gradient
+    # and Hessian column out to host memory, every step
+    host_models = [(m[0].cpu().numpy(), m[1].cpu().numpy()) for m in models]
+    q_host = q.cpu().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for pz in range(5):
+            Jh, Gh = acq.gradient(pz, *host_models[pz], q_host, scheme=FBN.LINEAR)
+            Hh = acq.hessian(pz, c, c)
+            Jh.cpu(), Gh.cpu(), Hh.cpu()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = 5 * (2 * w.nx * w.nz * 4 + q_host.nbytes)
+    d2h = 5 * (8 + 2 * w.nx * w.nz * 8 + 4 * w.nx * w.nz * 8)
+    # dominant kernel: the roofline of the FP32 pipe (bound "alu")
+    kern = prof["kernels"]
+    name = max(kern, key=lambda k: kern[k]["ms"])
+    per_launch_ms = kern[name]["ms"] / kern[name]["launches"]
+    flops = FB_FLOPS_PER_TERM * terms
+    sm_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(sm_mhz)
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    cpu = cpu_sample(w) if (cpu_sample and not args.no_cpu) else None
+    out = {
+        "metric": "Born W-terms/s (frequency x source x receiver x node products), Schemes I/II",
+        "value": round(passes * terms / (ms / 1e3) / 1e9, 3), "unit": "GW-terms/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "freq-born-paper-121x121", "grid": "121x121 nodes, dx 5 m, centred on x_0",
+                   "acquisition": "10 sources, 100 receivers, 490 m circle", "frequencies": "60 (0.25-15 Hz)",
+                   "step": "5 x (Scheme I gradient + Hessian column at x_0)",
+                   "l2": "Green tables 1.55 GB, larger than L2", "tables_ms": round(tables_ms, 1)},
+        "roofline": {"kernel": name, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "flops_per_launch": flops, "avg_launch_us": round(1e3 * per_launch_ms, 2),
+                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 flops x max SM clock"},
+        "kernels": kern, "gpu_launches": sum(v["launches"] for v in kern.values()) // max(args.steps, 1),
+        "clocks": clk,
+        "e2e": {"value": round(passes * terms / e2e_s / 1e9, 3), "unit": "GW-terms/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+

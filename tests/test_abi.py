@@ -57,3 +57,18 @@ def test_workspace_planning(L):
     bad = fwi.make_grid(601, 601, 5.0, 5e-4, 3000, order=6)
     with pytest.raises(fwi.FwiError):
         fwi.fwi_workspace_bytes(bad, 1, 1, fwi.OP_MODEL, 0)
+
+
+def test_fborn_workspace_planning(L):
+    from paper_1804_01184_gb300 import fborn, fwi
+    fwi._lib = None
+    fborn._bound = False
+    fg = fborn.make_fgrid(121, 121, 60, 5.0, -300.0, -300.0)
+    n = fborn.fwi_fborn_workspace_bytes(fg, 10, 100)
+    tables = 2 * 60 * 110 * 121 * 121 * 8
+    chunks = (121 * 121 + 127) // 128
+    assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + (1 << 16)
+    with pytest.raises(fwi.FwiError):
+        fborn.fwi_fborn_workspace_bytes(fborn.make_fgrid(121, 121, 0, 5.0, 0.0, 0.0), 10, 100)
+    with pytest.raises(fwi.FwiError):
+        fborn.fwi_fborn_workspace_bytes(fg, 0, 100)

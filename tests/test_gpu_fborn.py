@@ -1,0 +1,161 @@
+"""Frequency-domain Born modelling of Schemes I/II through the C ABI against the FP64 oracle
+(oracle/fborn.py): Green tables and Born data for every parameterization and both maps,
+the misfit and its gradient, the Scheme I Hessian column and reduced Hessian; tile edges
+(ragged node chunks, more than 16 sources, more than 128 receivers); the paper's full
+acquisition on sampled outputs; determinism and argument errors."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fborn as FB
+from paper_1804_01184_gb300 import inputs as I
+from tests._common import GRAD_TOL, TRACE_TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+HESS_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_01184_gb300 import build, fborn
+    build.build()
+    return fborn
+
+
+def ofg(w):
+    return FB.FGrid(**w.fgrid_kwargs())
+
+
+def crel(a, b):
+    """Relative L2 distance of complex arrays."""
+    a, b = np.asarray(a, np.complex128), np.asarray(b, np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_data(w, pz, a, b, scheme, incident=True):
+    return FB.model(ofg(w), w.freqs, w.spectrum, w.src_xy, w.rec_xy, pz, a, b, scheme, with_incident=incident)
+
+
+CASES = [dict(seed=0), dict(seed=5, nx=9, nz=7, ns=17, nr=130, nf=2)]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("pz", range(5))
+def test_born_data_matches_oracle(B, case, scheme, pz):
+    w = I.small_freq_case(pz=pz, **case)
+    acq = B.acquisition(w)
+    for incident in (True, False):
+        d = acq.model(pz, w.xi_a, w.xi_b, scheme=scheme, incident=incident).cpu().numpy()
+        ref = oracle_data(w, pz, w.xi_a, w.xi_b, scheme, incident)
+        assert crel(d, ref) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("pz", range(5))
+def test_gradient_matches_oracle(B, case, scheme, pz):
+    w = I.small_freq_case(pz=pz, **case)
+    acq = B.acquisition(w)
+    q = oracle_data(w, pz, 1.4 * w.xi_a, 0.6 * w.xi_b, 2).astype(np.complex64)
+    a0, b0 = 0.5 * w.xi_a, -0.3 * w.xi_b
+    J, G = acq.gradient(pz, a0, b0, q, scheme=scheme)
+    Jr, ga, gb = FB.gradient(ofg(w), w.freqs, w.spectrum, w.src_xy, w.rec_xy, pz, a0, b0,
+                             q.astype(np.complex128), scheme)
+    assert abs(J.item() - Jr) <= 1e-5 * Jr
+    G = G.cpu().numpy()
+    assert rel_l2(G[0], ga) <= GRAD_TOL
+    assert rel_l2(G[1], gb) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("pz", range(5))
+def test_hessian_column_matches_oracle(B, case, pz):
+    w = I.small_freq_case(pz=pz, **case)
+    acq = B.acquisition(w)
+    jx, jz = w.nx // 3, w.nz // 2
+    H = acq.hessian(pz, jx, jz).cpu().numpy()
+    ref = FB.hessian_column(ofg(w), w.freqs, w.spectrum, w.src_xy, w.rec_xy, pz, jz * w.nx + jx)
+    assert rel_l2(H, ref) <= HESS_TOL
+    for a in range(2):
+        for b in range(2):
+            assert rel_l2(H[a, b], ref[a, b]) <= 10 * HESS_TOL
+
+
+def test_reduced_hessian_cross_terms_paper_claim(B):
+    """With sources and receivers evenly around x_0 the K-rho and 1/K-1/rho reduced Hessians
+    have no cross-parameter term (to FP32 rounding); vp-rho, Ip-rho and vp-Ip do."""
+    w = I.freq_paper(n=21, nf=12, df=1.0)
+    acq = B.acquisition(w)
+    c = w.nx // 2
+    for pz in range(5):
+        H = acq.reduced_hessian(pz, c, c).cpu().numpy()
+        x = abs(H[0, 1]) / math.sqrt(H[0, 0] * H[1, 1])
+        assert abs(H[0, 1] - H[1, 0]) <= 1e-5 * abs(H).max()
+        assert (x < 1e-5) if pz in (3, 4) else (x > 0.1), (pz, x)
+
+
+def test_paper_acquisition_sampled(B):
+    """The benchmark's configuration (121 x 121 nodes, 60 frequencies, 10 sources, 100
+    receivers): data entries of a few (source, receiver) pairs at all frequencies against the
+    oracle run on those pairs alone; the gradient's directional derivative against a central
+    difference of GPU misfits (exact for the quadratic Scheme I misfit); the Hessian column at
+    x_0 against the oracle on two of the frequencies."""
+    w = I.freq_paper()
+    acq = B.acquisition(w)
+    d = acq.model(0, w.xi_a, w.xi_b, scheme=2).cpu().numpy()
+    ss, rr = [0, 3, 7], [0, 41, 99]
+    ref = FB.model(ofg(w), w.freqs, w.spectrum, w.src_xy[ss], w.rec_xy[rr], 0, w.xi_a, w.xi_b, 2)
+    got = d[:, ss][:, :, rr]
+    assert crel(got, ref) <= TRACE_TOL
+    # gradient along a direction, Scheme I (quadratic misfit)
+    q = acq.model(0, w.xi_a, w.xi_b, scheme=2)
+    a0 = np.zeros_like(w.xi_a)
+    _, G = acq.gradient(0, a0, a0, q, scheme=1)
+    G = G.cpu().numpy()
+    da = I.gaussian(w.nx, w.nz, w.dx, ((w.nx - 1) / 2 * w.dx, (w.nz - 1) / 2 * w.dx), 40.0)
+    db = 0.5 * da
+    eps = 0.05
+    Jp = acq.gradient(0, eps * da, eps * db, q, scheme=1)[0].item()
+    Jm = acq.gradient(0, -eps * da, -eps * db, q, scheme=1)[0].item()
+    slope = float(np.sum(G[0] * da) + np.sum(G[1] * db))
+    assert abs((Jp - Jm) / (2 * eps) - slope) <= 1e-3 * abs(slope)
+    # Hessian column at x_0 on two frequencies
+    sub = [9, 29]
+    w2 = I.freq_paper()
+    w2.freqs, w2.spectrum = w.freqs[sub], w.spectrum[sub]
+    acq2 = B.acquisition(w2)
+    c = w.nx // 2
+    H = acq2.hessian(3, c, c).cpu().numpy()
+    ref = FB.hessian_column(ofg(w2), w2.freqs, w2.spectrum, w2.src_xy, w2.rec_xy, 3, c * w.nx + c)
+    assert rel_l2(H, ref) <= HESS_TOL
+
+
+def test_deterministic_and_errors(B):
+    from paper_1804_01184_gb300 import fwi as F
+    w = I.small_freq_case(seed=7)
+    acq = B.acquisition(w)
+    d1 = acq.model(1, w.xi_a, w.xi_b).cpu().numpy()
+    d2 = acq.model(1, w.xi_a, w.xi_b).cpu().numpy()
+    np.testing.assert_array_equal(d1, d2)
+    _, g1 = acq.gradient(2, w.xi_a, w.xi_b, d1 * 0.9)
+    _, g2 = acq.gradient(2, w.xi_a, w.xi_b, d1 * 0.9)
+    np.testing.assert_array_equal(g1.cpu().numpy(), g2.cpu().numpy())
+    fg = B.make_fgrid(w.nx, w.nz, w.nf, w.dx, w.x0, w.z0)
+    on_node = w.src_xy.copy()
+    on_node[0] = (w.x0 + 2 * w.dx, w.z0 + 3 * w.dx)
+    with pytest.raises(F.FwiError):
+        B.Acquisition(fg, w.freqs, w.spectrum, on_node, w.rec_xy)
+    bad_f = w.freqs.copy()
+    bad_f[1] = 0.0
+    with pytest.raises(F.FwiError):
+        B.Acquisition(fg, bad_f, w.spectrum, w.src_xy, w.rec_xy)
+    with pytest.raises(F.FwiError):
+        acq.hessian(0, w.nx, 0)
+    with pytest.raises(F.FwiError):
+        acq.model(0, w.xi_a, w.xi_b, scheme=3)
