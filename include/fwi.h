@@ -338,6 +338,11 @@ int fwi_fborn_gradient(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param
                        const float *xi_b, const float *data_obs, void *work, double *misfit, double *grad,
                        void *stream);
 
+/* The misfit J alone (one double), as fwi_fborn_gradient computes it: the data contraction,
+ * the residual and the reduction, without the gradient pass (line searches). */
+int fwi_fborn_misfit(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param pz, const float *xi_a,
+                     const float *xi_b, const float *data_obs, void *work, double *misfit, void *stream);
+
 /* Scheme I Hessian terms H [2][2][nz][nx] (double): H[a][b][i] = d^2 J / d xi_a(x_i) d xi_b(x_j)
  * for the fixed node j = (jx, jz) and every node i -- the real part of
  * dx^4 sum_f |S_f|^2 sum_{s,r} conj(W_a(x_i)) W_b(x_j) taken through the linear map of pz (the

@@ -1,6 +1,6 @@
 """Binding of the frequency-domain Born calls of libfwi.so (Schemes I and II; C ABI in
 include/fwi.h): ``fwi_fborn_workspace_bytes``, ``fwi_fborn_tables``, ``fwi_fborn_model``,
-``fwi_fborn_gradient``, ``fwi_fborn_hessian``.
+``fwi_fborn_gradient``, ``fwi_fborn_misfit``, ``fwi_fborn_hessian``.
 
 Argument marshalling only: the Green tables, the Born contraction, the misfit, the gradient
 and the Hessian all run in the library's kernels.  ``Acquisition`` holds one workspace with
@@ -43,6 +43,7 @@ def lib():
         L.fwi_fborn_model.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
         L.fwi_fborn_gradient.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.fwi_fborn_hessian.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+        L.fwi_fborn_misfit.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
         _bound = True
     return L
 
@@ -111,6 +112,15 @@ class Acquisition:
                                           F._ptr(xb), F._ptr(q), F._ptr(self.work), F._ptr(misfit), F._ptr(grad),
                                           F._stream(stream)))
         return misfit, grad
+
+    def misfit(self, pz, xi_a, xi_b, data_obs, scheme=LINEAR, out=None, stream=None):
+        """Misfit [1] float64 alone (fwi_fborn_misfit)."""
+        xa, xb, q = F._dev(xi_a), F._dev(xi_b), _complex_dev(data_obs)
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device="cuda")
+        F._raise(lib().fwi_fborn_misfit(C.byref(self.fg), self.ns, self.nr, int(scheme), int(pz), F._ptr(xa),
+                                        F._ptr(xb), F._ptr(q), F._ptr(self.work), F._ptr(out), F._stream(stream)))
+        return out
 
     def hessian(self, pz, jx, jz, out=None, stream=None):
         """Scheme I Hessian terms H[a][b][nz][nx] for the fixed node (jx, jz)

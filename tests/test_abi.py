@@ -66,8 +66,9 @@ def test_fborn_workspace_planning(L):
     fg = fborn.make_fgrid(121, 121, 60, 5.0, -300.0, -300.0)
     n = fborn.fwi_fborn_workspace_bytes(fg, 10, 100)
     tables = 2 * 60 * 110 * 121 * 121 * 8
-    chunks = (121 * 121 + 127) // 128
-    assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + (1 << 16)
+    chunks = (121 * 121 + 255) // 256
+    freq_partials = 60 * 4 * 121 * 121 * 8
+    assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + freq_partials + (1 << 16)
     with pytest.raises(fwi.FwiError):
         fborn.fwi_fborn_workspace_bytes(fborn.make_fgrid(121, 121, 0, 5.0, 0.0, 0.0), 10, 100)
     with pytest.raises(fwi.FwiError):
