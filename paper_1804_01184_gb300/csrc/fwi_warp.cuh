@@ -235,9 +235,12 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
     const bool hsrc = strip_has_src(sc, sp.x0, z0, zend);
     // stage row g (rows f = f0 + g; r = f - M; j = f - 2M + 1) into ring slot ps, stage ss
+    // rows the strip's outputs depend on (the others stream in as zeros, reading nothing):
+    // p rows f >= z0 - 2M + 1, v_z rows r >= z0 - M, v_x / model rows j >= z0
     auto issue = [&](int g, int ps, int ss) {
         const int f = f0 + g, r = f - M, j = f - R + 1;
-        const bool vf = f >= 0 && f < d.Nz, vr = r >= 0 && r < d.Nz, vj = j >= 0 && j < d.Nz;
+        const bool vf = f >= max(0, z0 - R + 1) && f < d.Nz, vr = r >= max(0, z0 - M) && r < d.Nz,
+                   vj = j >= z0 && j < d.Nz;
         float *pr = ring[ps];
         float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
@@ -478,9 +481,13 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const float4 axe = ldg_if(mo.ax + L.ec, L.ein);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
+    // rows the strip's outputs depend on (the others stream in as zeros, reading nothing):
+    // pbar / K rows f >= z0 - 2M + 1, forward p rows f >= z0 - M + 1, u_z rows r >= z0 - M,
+    // u_x rows j >= z0
     auto issue = [&](int g, int ps, int ss) {
         const int f = f0 + g, r = f - M, j = f - R + 1;
-        const bool vf = f >= 0 && f < d.Nz, vr = r >= 0 && r < d.Nz, vj = j >= 0 && j < d.Nz;
+        const bool vf = f >= max(0, z0 - R + 1) && f < d.Nz, vr = r >= max(0, z0 - M) && r < d.Nz,
+                   vj = j >= z0 && j < d.Nz, vp = vf && f >= z0 - M + 1;
         float *prow = pr[ps];
         float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
@@ -489,11 +496,11 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
             cp4(&sh.scl[ss][1], mo.azh, r, vr);
             cp4(&sh.scl[ss][2], mo.az, j, vj);
         }
-        cp16(prow + L.mo, PN, of + L.mc, vf && L.in);
+        cp16(prow + L.mo, PN, of + L.mc, vp && L.in);
         cp16(sg[0] + L.mo, A0, of + L.mc, vf && L.in);
         cp16(sg[1] + L.mo, mo.K, of + L.mc, vf && L.in);
         if (!L.own) {
-            cp16(prow + L.eo, PN, of + L.ec, vf && L.ein);
+            cp16(prow + L.eo, PN, of + L.ec, vp && L.ein);
             cp16(sg[0] + L.eo, A0, of + L.ec, vf && L.ein);
             cp16(sg[1] + L.eo, mo.K, of + L.ec, vf && L.ein);
         }
@@ -694,9 +701,12 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
     const bool hsrc = strip_has_src(sc, sp.x0, z0, zend);
+    // rows the strip's outputs depend on (the others stream in as zeros, reading nothing):
+    // p, q rows f >= z0 - 2M + 1, v_z, u_z rows r >= z0 - M, v_x, u_x, model rows j >= z0
     auto issue = [&](int g, int ps, int ss) {
         const int f = f0 + g, r = f - M, j = f - R + 1;
-        const bool vf = f >= 0 && f < d.Nz, vr = r >= 0 && r < d.Nz, vj = j >= 0 && j < d.Nz;
+        const bool vf = f >= max(0, z0 - R + 1) && f < d.Nz, vr = r >= max(0, z0 - M) && r < d.Nz,
+                   vj = j >= z0 && j < d.Nz;
         float *pr = spr[ps], *qr = sqr[ps];
         float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
