@@ -65,7 +65,8 @@ def test_fborn_workspace_planning(L):
     fborn._bound = False
     fg = fborn.make_fgrid(121, 121, 60, 5.0, -300.0, -300.0)
     n = fborn.fwi_fborn_workspace_bytes(fg, 10, 100)
-    tables = 2 * 60 * 110 * 121 * 121 * 8
+    rows = (121 * 121 + 127) // 128 * 128      # table rows padded to 128 nodes
+    tables = 2 * 60 * 110 * rows * 8
     chunks = (121 * 121 + 255) // 256
     freq_partials = 60 * 4 * 121 * 121 * 8
     assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + freq_partials + (1 << 16)
