@@ -103,6 +103,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="fixed strip height of the streaming kernels (0: tuned online; profiling uses a fixed one)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="gradient workspace budget (0: 80%% of free device memory)")
     ap.add_argument("--workload", default="gaussian",
@@ -275,6 +277,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     fwi.lib()
+    if args.tile:
+        fwi.fwi_set_tile(args.tile, 0)
 
     nt, ns = args.nt, args.shots
     w0 = I.config_gaussian(0.3, "vp", nt=nt, ns=ns)
