@@ -5,7 +5,10 @@ wave equation: forward shots (``fwi_model``), Born modelling (``fwi_born``), and
 back-propagation with the zero-lag cross-correlation fused into the gradient for all five
 parameterizations of Table 1 (``fwi_adjoint``, ``fwi_gradient``).  The compute path is the
 CUDA library ``libfwi.so`` (C ABI declared in ``include/fwi.h``); ``paper_1804_01184_gb300.fwi``
-is its thin Python binding.  ``inputs`` holds the seeded synthetic workloads.
+is its thin Python binding.  ``inputs`` holds the seeded synthetic workloads.  ``fborn`` binds
+the frequency-domain Born path of the paper's Schemes I/II (analytic Green functions, Born
+data, misfit gradient, Hessian column); ``engine``, ``serve``, ``autograd``, ``bowls``,
+``invert`` and ``dist`` build on the library calls.
 
 The binding is imported lazily so that ``inputs`` can be used without a GPU.
 """
