@@ -485,6 +485,17 @@ def bench_fborn(args, Clocks, cpu_sample=None):
     peak = fp32_peak_tflops(sm_mhz)
     achieved = flops / (per_launch_ms / 1e3) / 1e12
     cpu = cpu_sample(w) if (cpu_sample and not args.no_cpu) else None
+    # the point-scatterer analysis (Sec. "Point-scatterer Analysis"): the reduced Hessian at x_0
+    # of each parameterization -- condition number, cross-parameter ratio, long-axis angle
+    names = ["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"]
+    reduced = {}
+    for pz in range(5):
+        Hr = H[pz, :, :, c, c].cpu().numpy()
+        Hs = 0.5 * (Hr + Hr.T)
+        lam, vec = np.linalg.eigh(Hs)
+        reduced[names[pz]] = {"condition": float(f"{lam[1] / lam[0]:.4g}"),
+                              "cross_ratio": float(f"{Hs[0, 1] / np.sqrt(Hs[0, 0] * Hs[1, 1]):.3g}"),
+                              "long_axis_deg": round(float(np.degrees(np.arctan2(vec[1, 0], vec[0, 0])) % 180.0), 1)}
     out = {
         "metric": "Born W-terms/s (frequency x source x receiver x node products), Schemes I/II",
         "value": round(passes * terms / (ms / 1e3) / 1e9, 3), "unit": "GW-terms/s", "n_gpus": 1,
@@ -503,6 +514,7 @@ def bench_fborn(args, Clocks, cpu_sample=None):
         "e2e": {"value": round(passes * terms / e2e_s / 1e9, 3), "unit": "GW-terms/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "cpu_baseline": cpu,
+        "reduced_hessian_x0": reduced,
     }
     print(json.dumps(out), flush=True)
 
