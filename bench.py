@@ -103,6 +103,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-every", type=int, default=8,
+                    help="time one launch in N of each kernel with CUDA events inside the timed region")
     ap.add_argument("--tile", type=int, default=0,
                     help="fixed strip height of the streaming kernels (0: tuned online; profiling uses a fixed one)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
@@ -329,7 +331,7 @@ def main():
 
     clocks = Clocks(local)
     clocks.start()
-    fwi.lib().fwi_profile(1)
+    fwi.lib().fwi_profile(max(1, args.profile_every))
     launches[0] = 0
     barrier()
     torch.cuda.synchronize(dev)
@@ -347,8 +349,9 @@ def main():
     fwi.lib().fwi_profile_report(buf, len(buf))
     prof = {}
     for line in buf.value.decode().splitlines():
-        name, cnt, tot = line.rsplit(" ", 2)
-        prof[name] = (int(cnt), float(tot))
+        name, seen, cnt, tot = line.rsplit(" ", 3)
+        # all launches of the kernel, and its device time estimated from the timed ones
+        prof[name] = (int(seen), float(tot) / int(cnt) * int(seen), int(cnt))
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -368,9 +371,9 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     total_dev = sum(v[1] for v in prof.values()) or 1.0
     kernels = {}
-    for name, (cnt, tot) in prof.items():
+    for name, (cnt, tot, timed) in prof.items():
         kernels[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = {
-            "launches": cnt, "ms": round(tot, 3), "share": round(tot / total_dev, 4)}
+            "launches": cnt, "timed_launches": timed, "ms": round(tot, 3), "share": round(tot / total_dev, 4)}
     # shot-steps each time-step kernel performs per bench step: the forward runs in fwi_model
     # and in fwi_gradient, the adjoint in fwi_gradient, Born in fwi_born
     shot_steps = {"k_fwd_warp": 2 * ns * nt, "k_adj_warp": ns * nt, "k_born_warp": ns * nt}
@@ -378,7 +381,7 @@ def main():
     dom = max(((n, v) for n, v in prof.items() if short_name(n) in KERNEL_BYTES), key=lambda kv: kv[1][1],
               default=None)
     if dom:
-        name, (cnt, tot) = dom
+        name, (cnt, tot, _) = dom
         short = short_name(name)
         shots = shot_steps[short] * args.steps / cnt          # average shots per launch
         bytes_per_launch = cells * (KERNEL_BYTES[short] * shots + MODEL_BYTES[short])

@@ -269,10 +269,13 @@ int fwi_engine_info(fwi_engine *engine, int *queued, int *running, int *pending,
 /* Waits for the engine's stream and frees the engine (not the arena). */
 int fwi_engine_destroy(fwi_engine *engine);
 
-/* Per-launch timing (no counterpart in the paper: measurement support).  While enabled,
- * every kernel launch of the library is bracketed by a CUDA event pair recorded on the
- * launching stream.  fwi_profile_report() waits for those events, writes one line per kernel
- * "name launches total_ms\n" into buf (at most len bytes, NUL-terminated), resets the
+/* Per-launch timing (no counterpart in the paper: measurement support).  While enabled
+ * (enable = 1), every kernel launch of the library is bracketed by a CUDA event pair recorded
+ * on the launching stream; enable = N > 1 samples one launch in N of each kernel (the first of
+ * every N since the call), which keeps the events' own cost off a timed loop; 0 disables.
+ * fwi_profile_report() waits for those events, writes one line per kernel
+ * "name launches timed_launches timed_ms\n" (launches since profiling was enabled or last
+ * reported; the device time summed over the timed ones) into buf (at most len bytes, NUL-terminated), resets the
  * record and returns the report length (or a negative FWI_E* code). */
 int fwi_profile(int enable);
 int fwi_profile_report(char *buf, size_t len);

@@ -59,11 +59,17 @@ struct Profiler {
         names.emplace_back(name);
         return k;
     }
-    // returns the event pair for the next launch, or nullptr if profiling is off
+    int every = 1;                   // time one launch in `every` of each kernel
+    std::vector<long long> seen;     // launches of kernel k since profiling was enabled
+    // returns the event pair for the next launch, or nullptr if profiling is off (or this
+    // launch is not sampled)
     cudaEvent_t *next(const char *name)
     {
         if (!on) return nullptr;
         std::lock_guard<std::mutex> lk(mu);
+        const int k = id(name);
+        if ((int)seen.size() <= k) seen.resize(k + 1, 0);
+        if (seen[k]++ % every) return nullptr;
         if (2 * (used + 1) > ev.size()) {
             size_t add = std::max<size_t>(1024, ev.size());
             for (size_t k = 0; k < add; ++k) {
@@ -73,7 +79,7 @@ struct Profiler {
             }
         }
         kind.resize(used + 1);
-        kind[used] = id(name);
+        kind[used] = k;
         return &ev[2 * used++];
     }
 };
@@ -974,8 +980,11 @@ int fwi_set_tile(int tz, int variant)
 
 int fwi_profile(int enable)
 {
+    if (enable < 0) return fail(FWI_EINVAL, "profile sampling period must be >= 0");
     std::lock_guard<std::mutex> lk(g_prof.mu);
     g_prof.on = enable != 0;
+    g_prof.every = enable > 1 ? enable : 1;
+    if (enable) g_prof.seen.assign(g_prof.seen.size(), 0);   // disabling keeps the counts for the report
     return FWI_OK;
 }
 
@@ -998,9 +1007,11 @@ int fwi_profile_report(char *buf, size_t len)
     char line[256];
     for (size_t k = 0; k < g_prof.names.size(); ++k) {
         if (!cnt[k]) continue;
-        snprintf(line, sizeof line, "%s %lld %.6f\n", g_prof.names[k].c_str(), cnt[k], ms[k]);
+        const long long seen = k < g_prof.seen.size() ? g_prof.seen[k] : cnt[k];
+        snprintf(line, sizeof line, "%s %lld %lld %.6f\n", g_prof.names[k].c_str(), seen, cnt[k], ms[k]);
         out += line;
     }
+    g_prof.seen.assign(g_prof.seen.size(), 0);
     if (buf && len) {
         strncpy(buf, out.c_str(), len - 1);
         buf[len - 1] = 0;

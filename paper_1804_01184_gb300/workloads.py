@@ -36,7 +36,7 @@ def kernel_profile(enable):
     L.fwi_profile(0)
     prof = {}
     for line in buf.value.decode().splitlines():
-        name, cnt, tot = line.rsplit(" ", 2)
+        name, _, cnt, tot = line.rsplit(" ", 3)
         prof[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = (int(cnt), float(tot))
     total = sum(v[1] for v in prof.values()) or 1.0
     return {"device_ms": round(total, 1),
