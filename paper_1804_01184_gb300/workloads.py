@@ -24,20 +24,22 @@ PASSES = {E.JOB_MODEL: 1, E.JOB_BORN: 1, E.JOB_GRADIENT: 2}
 OPS = {E.JOB_MODEL: F.OP_MODEL, E.JOB_BORN: F.OP_BORN, E.JOB_GRADIENT: F.OP_GRADIENT}
 
 
-def kernel_profile(enable):
-    """Per-kernel device time recorded by the library's launch events (fwi_profile)."""
+def kernel_profile(enable, every=1):
+    """Per-kernel device time recorded by the library's launch events (fwi_profile), one launch
+    in `every` of each kernel timed; a kernel's time is its timed mean times its launches."""
     import ctypes
     L = F.lib()
     if enable:
-        L.fwi_profile(1)
+        L.fwi_profile(int(every))
         return None
     buf = ctypes.create_string_buffer(1 << 16)
     L.fwi_profile_report(buf, len(buf))
     L.fwi_profile(0)
     prof = {}
     for line in buf.value.decode().splitlines():
-        name, _, cnt, tot = line.rsplit(" ", 3)
-        prof[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = (int(cnt), float(tot))
+        name, seen, cnt, tot = line.rsplit(" ", 3)
+        prof[name.replace("fwi::", "").replace("(", "").replace(")", "").replace(", ", ",")] = (
+            int(seen), float(tot) / int(cnt) * int(seen))
     total = sum(v[1] for v in prof.values()) or 1.0
     return {"device_ms": round(total, 1),
             "kernels": {k: {"launches": c, "ms": round(t, 1), "share": round(t / total, 4)}
@@ -82,7 +84,7 @@ def bench_batch(args, Clocks):
     clocks = Clocks(0)
     clocks.start()
     if args.profile:
-        kernel_profile(True)
+        kernel_profile(True, every=8)
     # phase A: observed data of the true models (all shots of a job in one group when it fits)
     tickets = [eng.submit_model(grid_of(w), w.pz, s["a"], s["b"], s["src"], s["wav"], s["rec"],
                                 work_budget=min(grad_budget, 1 << 62)) for w, s in zip(jobs, staged)]
@@ -208,7 +210,7 @@ def bench_serve(args, Clocks):
     clocks = Clocks(0)
     clocks.start()
     if args.profile:
-        kernel_profile(True)
+        kernel_profile(True, every=8)
     stats, _ = S.serve(reqs, arrivals, arena)
     prof = kernel_profile(False) if args.profile else None
     clk = clocks.stop()
