@@ -331,3 +331,30 @@ def test_register_capped_variants_are_bitwise_identical(F, variant):
     np.testing.assert_array_equal(out[1][1], out[0][1])
     assert out[1][2] == out[0][2]
     np.testing.assert_array_equal(out[1][3], out[0][3])
+
+
+def test_profile_sampling_counts_every_launch_and_times_one_in_n(F):
+    """fwi_profile(N) times the first of every N launches of each kernel and still counts them
+    all: the report's launches equal the library's launch count, the timed ones ceil(n / N)."""
+    import ctypes
+    w = I.small_case(seed=2, nx=40, nz=36, nt=37, order=8, sponge=6, ns=2, nr=5)
+    g = gpu_grid(w)
+    F.fwi_model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)     # plans, tuner state
+    torch.cuda.synchronize()
+    L = F.lib()
+    L.fwi_profile(4)
+    F.launch_count()
+    F.fwi_model(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    launched = F.launch_count()
+    torch.cuda.synchronize()
+    L.fwi_profile(0)
+    buf = ctypes.create_string_buffer(1 << 16)
+    assert L.fwi_profile_report(buf, len(buf)) > 0
+    total = 0
+    for line in buf.value.decode().splitlines():
+        name, seen, timed, ms = line.rsplit(" ", 3)
+        seen, timed = int(seen), int(timed)
+        assert timed == (seen + 3) // 4, line
+        assert float(ms) > 0
+        total += seen
+    assert total == launched
