@@ -10,7 +10,8 @@ gradient method converges in that parameterization (circular: fast; elongated at
 degrees: slow).
 
 The scatterers of Table "tab:param_scat" whose shape is known: (i) point, vp only; (ii)
-Gaussian, vp only; (iv) point, rho only; (v) Gaussian, rho only.
+Gaussian, vp only; (iv) point, rho only; (v) Gaussian, rho only (the inversions of
+``invert`` also take the unknown-shape ones, (iii), (vi) and (vii)).
 """
 from __future__ import annotations
 
@@ -38,6 +39,32 @@ def scatterer(case, amplitude=0.2, nt=1400):
     else:
         g = I.gaussian(w.nx, w.nz, w.dx, I.centre_of(w.nx, w.nz, w.dx), 50.0)
     return w, g
+
+
+# The scatterers of Table "tab:param_scat" whose shape is unknown to the inversion: (iii)
+# Gaussian, vp only; (vi) Gaussian, rho only; (vii) Gaussian with no bulk-modulus contrast
+# ((1 + xi_rho)(1 + xi_vp)^2 = 1, xi_vp the Gaussian).
+UNKNOWN = {"iii": "vp", "vi": "rho", "vii": "nonK"}
+
+
+def unknown_contrasts(g, kind, amplitude=0.2):
+    """True (xi_vp, xi_rho) float32 fields of an unknown-shape scatterer of unit shape g."""
+    a = (np.float32(amplitude) * g).astype(np.float32)
+    z = np.zeros_like(a)
+    if kind == "vp":
+        return a, z
+    if kind == "rho":
+        return z, a
+    return a, (1.0 / (1.0 + a.astype(np.float64)) ** 2 - 1.0).astype(np.float32)
+
+
+def unknown_scatterer(case, amplitude=0.2, nt=1400):
+    """The paper's acquisition around unknown-shape scatterer `case` (Gaussian, sigma 50 m):
+    the workload with its true vp-rho contrasts."""
+    w = I.config_paper(nt=nt, which="vp", amplitude=amplitude)
+    g = I.gaussian(w.nx, w.nz, w.dx, I.centre_of(w.nx, w.nz, w.dx), 50.0)
+    w.xi_a, w.xi_b = unknown_contrasts(g, UNKNOWN[case], amplitude)
+    return w
 
 
 def true_point(pz, dvp, drho):

@@ -311,6 +311,8 @@ def bench_bowls(args, Clocks):
     from . import bowls as B
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.case not in B.CASES:
+        raise SystemExit("error bowls need a known-shape scatterer: --case i, ii, iv or v")
     w, g = B.scatterer(args.case)
     shape, which = B.CASES[args.case]
     amp = 0.2
@@ -365,32 +367,48 @@ def bench_invert(args, Clocks):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     names = ["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"]
+    known = args.case in B.CASES
+    kind = "known-shape" if known else "unknown-shape"
     if args.scheme in (1, 2):
         from . import fborn as FBN
-        shape, which = B.CASES[args.case]
-        w = I.freq_paper(which=which, shape=shape)
-        g = (I.point(w.nx, w.nz) if shape == "point"
-             else I.gaussian(w.nx, w.nz, w.dx, ((w.nx - 1) / 2 * w.dx, (w.nz - 1) / 2 * w.dx), 50.0))
+        if known:
+            shape, which = B.CASES[args.case]
+            w = I.freq_paper(which=which, shape=shape)
+            g = (I.point(w.nx, w.nz) if shape == "point"
+                 else I.gaussian(w.nx, w.nz, w.dx, ((w.nx - 1) / 2 * w.dx, (w.nz - 1) / 2 * w.dx), 50.0))
+        else:
+            w = I.freq_paper()
+            gu = I.gaussian(w.nx, w.nz, w.dx, ((w.nx - 1) / 2 * w.dx, (w.nz - 1) / 2 * w.dx), 50.0)
+            w.xi_a, w.xi_b = B.unknown_contrasts(gu, B.UNKNOWN[args.case])
+            g = None
         acq = FBN.acquisition(w)
         data = acq.model(I.PZ_VP_RHO, w.xi_a, w.xi_b, scheme=FBN.NONLINEAR)
         make = lambda pz: V.BornInversion(acq, pz, data, args.scheme, shape=g)
         line_search = "8 trial steps a iteration (fwi_fborn_misfit)"
-        label = f"invert-scheme{args.scheme}-scatterer-{args.case}-known-shape"
+        label = f"invert-scheme{args.scheme}-scatterer-{args.case}-{kind}"
     else:
-        w, g = B.scatterer(args.case)
+        if known:
+            w, g = B.scatterer(args.case)
+        else:
+            w, g = B.unknown_scatterer(args.case), None
         data = F.fwi_model(grid_of(w), I.PZ_VP_RHO, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
         make = lambda pz: V.Inversion(w, pz, data, shape=g)
         line_search = "8 trial steps a iteration as engine jobs"
-        label = f"invert-scatterer-{args.case}-known-shape"
+        label = f"invert-scatterer-{args.case}-{kind}"
+    zero = lambda: torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)
+    m0 = (lambda: (0.0, 0.0)) if known else (lambda: (zero(), zero()))
     clocks = Clocks(0)
     clocks.start()
     t0 = time.perf_counter()
     res = {}
     for pz in range(5):
         inv = make(pz)
-        m, hist = inv.run((0.0, 0.0), iters=args.iters)
+        m, hist = inv.run(m0(), iters=args.iters)
         inv.close()
-        res[names[pz]] = {"final": [round(m[0], 5), round(m[1], 5)], "misfit": [float(f"{j:.5g}") for j in hist],
+        final = ([round(m[0], 5), round(m[1], 5)] if known else
+                 [round(float(m[0].abs().max()), 5), round(float(m[1].abs().max()), 5)])
+        res[names[pz]] = {("final" if known else "final_max_abs"): final,
+                          "misfit": [float(f"{j:.5g}") for j in hist],
                           "reduction": float(f"{hist[-1] / hist[0]:.4g}")}
     wall = time.perf_counter() - t0
     clk = clocks.stop()
