@@ -178,3 +178,30 @@ def test_born_inversions_converge(B):
         assert all(b < a for a, b in zip(hist, hist[1:]))
         assert hist[-1] < 1e-3 * hist[0], (pz, hist)
         assert np.hypot(m[0] - truth[0], m[1] - truth[1]) < 0.01, (pz, m)
+
+
+def test_degenerate_cases(B):
+    """Zero contrasts leave only the direct field (the scattered part is exactly zero); at the
+    model that generated the data the residual is the data's FP32 rounding alone, so the misfit
+    and the gradient vanish to that level; a single node, source and receiver work."""
+    w = I.small_freq_case(seed=11)
+    acq = B.acquisition(w)
+    z = np.zeros_like(w.xi_a)
+    assert not acq.model(2, z, z, incident=False).abs().max().item()
+    direct = acq.model(2, z, z).cpu().numpy()
+    ref = FB.model(ofg(w), w.freqs, w.spectrum, w.src_xy, w.rec_xy, 2, z, z, 2)
+    assert crel(direct, ref) <= TRACE_TOL
+    for scheme in (1, 2):
+        q = acq.model(3, w.xi_a, w.xi_b, scheme=scheme)
+        J, G = acq.gradient(3, w.xi_a, w.xi_b, q, scheme=scheme)
+        J1, G1 = acq.gradient(3, 0.9 * w.xi_a, 0.9 * w.xi_b, q, scheme=scheme)
+        assert J.item() <= 1e-10 * 0.5 * (q.abs() ** 2).sum().item()
+        assert G.abs().max().item() <= 1e-4 * G1.abs().max().item()
+    one = I.small_freq_case(seed=12, nx=1, nz=1, ns=1, nr=1, nf=1)
+    a1 = B.acquisition(one)
+    d = a1.model(0, one.xi_a, one.xi_b, scheme=2).cpu().numpy()
+    ref = FB.model(ofg(one), one.freqs, one.spectrum, one.src_xy, one.rec_xy, 0, one.xi_a, one.xi_b, 2)
+    assert crel(d, ref) <= TRACE_TOL
+    H = a1.hessian(4, 0, 0).cpu().numpy()
+    refH = FB.hessian_column(ofg(one), one.freqs, one.spectrum, one.src_xy, one.rec_xy, 4, 0)
+    assert rel_l2(H, refH) <= HESS_TOL
