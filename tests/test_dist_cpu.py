@@ -30,6 +30,41 @@ def case():
     return w, g, data
 
 
+def fcase():
+    from oracle import fborn as FB
+    w = I.small_freq_case(seed=71, nx=11, nz=9, ns=3, nr=5, nf=5, pz=I.PZ_VP_IP)
+    fg = FB.FGrid(**w.fgrid_kwargs())
+    q = FB.model(fg, w.freqs, w.spectrum, w.src_xy, w.rec_xy, w.pz, 1.2 * w.xi_a, 0.7 * w.xi_b, FB.NONLINEAR)
+    return w, fg, q
+
+
+def fworker(rank, world, port, out):
+    import torch.distributed as dist
+
+    from oracle import fborn as FB
+    from paper_1804_01184_gb300.dist import sharded_frequency_gradient
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    w, fg, q = fcase()
+    try:
+        def local(fr, sp, d):
+            if len(fr) == 0:
+                return 0.0, np.zeros((2, w.nz, w.nx))
+            J, ga, gb = FB.gradient(fg, fr, sp, w.src_xy, w.rec_xy, w.pz, w.xi_a, w.xi_b, d, FB.LINEAR)
+            return J, np.stack([ga, gb])
+
+        J, G = sharded_frequency_gradient(local, w.freqs, w.spectrum, q)
+        out.put((rank, "ok", J, G.numpy()))
+    except Exception as e:   # noqa: BLE001 - reported to the parent
+        out.put((rank, "error", repr(e), None))
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:   # noqa: BLE001
+            pass
+
+
 def worker(rank, world, port, out, fail_rank):
     import torch
     import torch.distributed as dist
@@ -59,11 +94,12 @@ def worker(rank, world, port, out, fail_rank):
             pass
 
 
-def run(world, fail_rank=-1):
+def run(world, fail_rank=-1, target=None):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = free_port()
-    procs = [ctx.Process(target=worker, args=(r, world, port, q, fail_rank)) for r in range(world)]
+    procs = [ctx.Process(target=target, args=(r, world, port, q)) if target else
+             ctx.Process(target=worker, args=(r, world, port, q, fail_rank)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=120) for _ in range(world)]
@@ -95,3 +131,16 @@ def test_failed_rank_is_detected():
     res = run(2, fail_rank=1)
     assert res[1][1] == "error" and "injected" in res[1][2]
     assert res[0][1] == "error"      # the surviving rank's all-reduce fails (peer gone / timeout)
+
+
+def test_frequency_sharded_born_gradient_equals_single_process():
+    """Schemes I/II: two gloo ranks each take half of the frequencies (the FP64 frequency-domain
+    oracle on its part); the all-reduced misfit and gradient equal the single-process ones."""
+    from oracle import fborn as FB
+    w, fg, q = fcase()
+    J, ga, gb = FB.gradient(fg, w.freqs, w.spectrum, w.src_xy, w.rec_xy, w.pz, w.xi_a, w.xi_b, q, FB.LINEAR)
+    G = np.stack([ga, gb])
+    for rank, status, Jr, Gr in run(2, target=fworker):
+        assert status == "ok", Jr
+        assert abs(Jr - J) <= 1e-12 * J
+        np.testing.assert_allclose(Gr, G, rtol=1e-10, atol=1e-12 * np.abs(G).max())
