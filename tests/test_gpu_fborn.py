@@ -205,3 +205,23 @@ def test_degenerate_cases(B):
     H = a1.hessian(4, 0, 0).cpu().numpy()
     refH = FB.hessian_column(ofg(one), one.freqs, one.spectrum, one.src_xy, one.rec_xy, 4, 0)
     assert rel_l2(H, refH) <= HESS_TOL
+
+
+def test_diffraction_patterns(B):
+    """Sec. "Diffraction-pattern Analysis": a unit point contrast at x_0 with sources and
+    receivers on a circle around it scatters the same energy at every angle for 1/K (and K, and
+    vp in vp-rho, whose maps keep only the bulk-modulus term) and as cos^2 of the scattering
+    angle for 1/rho (and rho in K-rho); the patterns do not depend on the sign of the map."""
+    from paper_1804_01184_gb300 import patterns as PT
+    w = I.freq_paper(n=21, nf=8, df=1.0)
+    acq = B.acquisition(w)
+    c = w.nx // 2
+    ang = PT.scattering_angles(w.src_xy, w.rec_xy, (0.0, 0.0))
+    for pz, param in ((4, 0), (3, 0), (0, 0)):
+        e = PT.diffraction_pattern(acq, pz, param, c, c)
+        assert e.std() <= 1e-5 * e.mean(), (pz, param)
+    for pz in (4, 3):
+        e = PT.diffraction_pattern(acq, pz, 1, c, c)
+        np.testing.assert_allclose(e / e.max(), PT.cos2(ang) / PT.cos2(ang).max(), atol=2e-5)
+    s = PT.pattern_summary(PT.diffraction_pattern(acq, 4, 1, c, c), ang)
+    assert s["90"] < 0.01 and s["0"] > 0.98 and s["180"] > 0.98
