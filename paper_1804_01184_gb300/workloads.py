@@ -505,6 +505,16 @@ def bench_fborn(args, Clocks, cpu_sample=None):
     peak = fp32_peak_tflops(sm_mhz)
     achieved = flops / (per_launch_ms / 1e3) / 1e12
     cpu = cpu_sample(w) if (cpu_sample and not args.no_cpu) else None
+    # diffraction patterns (Sec. "Diffraction-pattern Analysis"): energy scattered by a unit
+    # point contrast of each parameter at x_0, relative to its maximum, by scattering angle
+    from . import patterns as PT
+    ang = PT.scattering_angles(w.src_xy, w.rec_xy, (0.0, 0.0))
+    pnames = [("vp", "rho"), ("Ip", "rho"), ("vp", "Ip"), ("K", "rho"), ("1/K", "1/rho")]
+    patterns = {}
+    for pz in range(5):
+        for k in range(2):
+            patterns[f"{pnames[pz][k]} in {['vp-rho', 'Ip-rho', 'vp-Ip', 'K-rho', '1/K-1/rho'][pz]}"] = \
+                PT.pattern_summary(PT.diffraction_pattern(acq, pz, k, c, c), ang)
     # the point-scatterer analysis (Sec. "Point-scatterer Analysis"): the reduced Hessian at x_0
     # of each parameterization -- condition number, cross-parameter ratio, long-axis angle
     names = ["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"]
@@ -535,6 +545,7 @@ def bench_fborn(args, Clocks, cpu_sample=None):
                 "d2h_bytes_per_step": d2h},
         "cpu_baseline": cpu,
         "reduced_hessian_x0": reduced,
+        "diffraction_patterns": patterns,
     }
     print(json.dumps(out), flush=True)
 
