@@ -113,7 +113,8 @@ def parse():
                     choices=["gaussian", "batch", "serve", "differentiation", "bowls", "invert", "fborn"])
     ap.add_argument("--iters", type=int, default=15, help="invert: iterations")
     ap.add_argument("--scheme", type=int, default=3, choices=[1, 2, 3],
-                    help="invert: 3 time-domain modelling (Scheme III); 1, 2 frequency-domain Born (Schemes I, II)")
+                    help="invert / bowls: 3 time-domain modelling (Scheme III); 1, 2 frequency-domain Born "
+                         "(Schemes I, II)")
     ap.add_argument("--case", default="ii", choices=["i", "ii", "iii", "iv", "v", "vi", "vii"],
                     help="bowls / invert: scatterer (iii, vi, vii: unknown shape, invert only)")
     ap.add_argument("--bowl-n", type=int, default=21, help="bowls: contrasts per axis")

@@ -158,3 +158,15 @@ def bowl_shape(J, grid_a, grid_b, half=2):
     i0, j0 = np.unravel_index(int(np.argmin(J)), J.shape)
     return dict(argmin=(float(grid_a[i0]), float(grid_b[j0])), J_min=float(J[i0, j0]), condition=cond,
                 angle_deg=angle)
+
+
+def born_error_bowl(acq, g, pz, data, grid_a, grid_b, scheme):
+    """Schemes I/II: J[ia][ib] (float64 numpy) of the frequency-domain Born misfit for contrasts
+    (grid_a[ia] g, grid_b[ib] g) of parameterization pz under the map of `scheme`, against
+    data [nf][ns][nr] (fwi_fborn_misfit for every grid point)."""
+    gg = torch.as_tensor(np.ascontiguousarray(g)).cuda()
+    J = torch.empty((len(grid_a), len(grid_b)), dtype=torch.float64, device="cuda")
+    for ia, a in enumerate(grid_a):
+        for ib, b in enumerate(grid_b):
+            acq.misfit(pz, gg * float(a), gg * float(b), data, scheme=scheme, out=J[ia, ib:ib + 1])
+    return J.cpu().numpy()

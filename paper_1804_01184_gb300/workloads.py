@@ -313,6 +313,8 @@ def bench_bowls(args, Clocks):
     torch.cuda.set_device(dev)
     if args.case not in B.CASES:
         raise SystemExit("error bowls need a known-shape scatterer: --case i, ii, iv or v")
+    if args.scheme in (1, 2):
+        return bench_born_bowls(args, Clocks)
     w, g = B.scatterer(args.case)
     shape, which = B.CASES[args.case]
     amp = 0.2
@@ -349,6 +351,51 @@ def bench_bowls(args, Clocks):
                    "grid": "121x121 + 40-cell sponge, dx 10 m, 8th order, 1400 steps, 10 shots, 100 receivers, 5 Hz",
                    "bowl": f"{args.bowl_n}x{args.bowl_n} contrasts per parameterization, 5 parameterizations"},
         "solves_per_s": round(solves / wall, 2), "bowls": shapes, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def bench_born_bowls(args, Clocks):
+    """Error bowls of scatterer `args.case` under Schemes I/II: the frequency-domain Born misfit
+    (paper acquisition, 121 x 121 nodes at 5 m, 60 frequencies) over the same contrast grids as
+    the time-domain bowls; observed data from the exact map."""
+    from . import bowls as B
+    from . import fborn as FBN
+    if args.aperture != "all":
+        raise SystemExit("the frequency-domain bowls use every scattering angle")
+    shape, which = B.CASES[args.case]
+    w = I.freq_paper(which=which, shape=shape)
+    h = (w.nx - 1) / 2 * w.dx
+    g = I.point(w.nx, w.nz) if shape == "point" else I.gaussian(w.nx, w.nz, w.dx, (h, h), 50.0)
+    acq = FBN.acquisition(w)
+    data = acq.model(I.PZ_VP_RHO, w.xi_a, w.xi_b, scheme=FBN.NONLINEAR)
+    amp = 0.2
+    dvp, drho = (amp, 0.0) if which == "vp" else (0.0, amp)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    shapes = {}
+    for pz in range(5):
+        ta, tb = B.true_point(pz, dvp, drho)
+        ga, gb = B.grid_around(ta, args.bowl_n), B.grid_around(tb, args.bowl_n)
+        J = B.born_error_bowl(acq, g, pz, data, ga, gb, args.scheme)
+        shapes[["vp-rho", "Ip-rho", "vp-Ip", "K-rho", "1/K-1/rho"][pz]] = {
+            k: (round(v, 4) if isinstance(v, float) else [round(x, 4) for x in v])
+            for k, v in B.bowl_shape(J, ga, gb).items()}
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    points = 5 * args.bowl_n ** 2
+    out = {
+        "metric": "Born W-terms/s (frequency x source x receiver x node products), Schemes I/II",
+        "value": round(points * w.terms() / wall / 1e9, 3), "unit": "GW-terms/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": round(1e3 * wall, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"born-bowls-scheme{args.scheme}-scatterer-{args.case}",
+                   "scatterer": f"{shape}, {which} only, contrast {amp}",
+                   "grid": "121x121 nodes, dx 5 m, 10 sources, 100 receivers, 60 frequencies",
+                   "bowl": f"{args.bowl_n}x{args.bowl_n} contrasts per parameterization, 5 parameterizations"},
+        "misfits_per_s": round(points / wall, 1), "bowls": shapes, "clocks": clk,
     }
     print(json.dumps(out), flush=True)
 

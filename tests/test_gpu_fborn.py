@@ -225,3 +225,21 @@ def test_diffraction_patterns(B):
         np.testing.assert_allclose(e / e.max(), PT.cos2(ang) / PT.cos2(ang).max(), atol=2e-5)
     s = PT.pattern_summary(PT.diffraction_pattern(acq, 4, 1, c, c), ang)
     assert s["90"] < 0.01 and s["0"] > 0.98 and s["180"] > 0.98
+
+
+def test_born_error_bowl_vanishes_at_truth(B):
+    """Scheme II error bowl of a Gaussian vp scatterer in vp-rho: the contrast grid holds the
+    truth (0.2, 0), where the misfit falls to the data's rounding level, and it is the bowl's
+    minimum; every other point is far above it."""
+    from paper_1804_01184_gb300 import bowls as BW
+    w = I.freq_paper(n=31, nf=10, df=1.0)
+    h = (w.nx - 1) / 2 * w.dx
+    g = I.gaussian(w.nx, w.nz, w.dx, (h, h), 50.0)
+    acq = B.acquisition(w)
+    data = acq.model(0, np.float32(0.2) * g, 0 * g, scheme=2)
+    ga, gb = BW.grid_around(0.2, 7), BW.grid_around(0.0, 7)
+    J = BW.born_error_bowl(acq, g, 0, data, ga, gb, 2)
+    ia, ib = np.unravel_index(np.argmin(J), J.shape)
+    assert abs(ga[ia] - 0.2) < 1e-12 and abs(gb[ib]) < 1e-12
+    rest = np.delete(J.ravel(), np.argmin(J))
+    assert J.min() <= 1e-8 * rest.min()
