@@ -42,7 +42,7 @@ extern "C" {
 #define FWI_EINVAL   -1   /* bad size, null pointer, 1 + xi <= 0, position off the grid */
 #define FWI_ECFL     -2   /* dt above the stability limit of the stencil for the model */
 #define FWI_ENOMEM   -3   /* workspace smaller than the operation's minimum             */
-#define FWI_ETIMEOUT -4   /* a bounded device-side wait expired                         */
+#define FWI_ETIMEOUT -4   /* reserved for bounded device-side waits; no call returns it */
 #define FWI_ECUDA    -5   /* a CUDA runtime call failed                                 */
 
 /* Parameterizations of Table 1; contrasts xi = (m - m_o)/m_o of the named pair. */
@@ -113,8 +113,11 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
  * second), evaluated at the model (pz, xi_a, xi_b).  The adjoint wavefield is
  * cross-correlated with the forward wavefield at every step inside the adjoint kernels
  * (Sec. "Modelling and Inversion": gradient by adjoint modelling, then the chain rule).
- * Per-shot, per-step products accumulate in FP32; sums over shots, the density chain rule
- * and the parameterization chain rules run in FP64. */
+ * Accumulation: each adjoint step's products go into FP32 per-shot fields; after every
+ * chunk of steps (64 by default, fwi_set_accumulation) and after the last step those fields
+ * are flushed into FP64 running sums over shots (a fixed order: results are bitwise
+ * reproducible) and cleared, so no FP32 sum spans more than one chunk.  The density chain
+ * rule and the parameterization chain rules run in FP64. */
 int fwi_adjoint(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
                 const fwi_sources *src, const fwi_receivers *rec, const float *residual,
                 double *grads, void *work, size_t work_bytes, void *stream);
@@ -175,12 +178,18 @@ long long fwi_launch_count(void);
  *    contents; the call clears what must start at zero.  Calls whose work overlaps on the
  *    GPU (different streams, or different host threads) race on the scratch: serialise them.
  *  - The data-dependent checks fwi_model records in its workspace (1 + xi <= 0, CFL, points
- *    off the grid) land in the scratch, which fwi_status() cannot reach: validate those
- *    inputs beforehand.  Host-visible argument errors are returned as usual.
+ *    off the grid) land in the scratch; fwi_status_noalloc() reads them.  Host-visible
+ *    argument errors are returned as usual.
  */
 #define FWI_NOALLOC_SCRATCH_BYTES (64u << 20)
 int fwi_model_noalloc(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
                       const fwi_sources *src, const fwi_receivers *rec, float *traces, void *stream);
+
+/* fwi_status for fwi_model_noalloc (no counterpart in the paper): waits for `stream` and
+ * returns the data-dependent status the last fwi_model_noalloc call on the current device
+ * recorded in the built-in scratch (FWI_OK, FWI_EINVAL, FWI_ECFL), then clears it; FWI_OK
+ * when no such call has run on this device.  Allocates nothing. */
+int fwi_status_noalloc(void *stream);
 
 /* Wavefield checkpointing (no counterpart in the paper: the adjoint needs the forward
  * wavefield, Sec. "Scheme III").  every > 0: plans made afterwards for fwi_adjoint and
@@ -189,6 +198,14 @@ int fwi_model_noalloc(const fwi_grid *g, fwi_param pz, const float *xi_a, const 
  * keeps the whole history when it fits and otherwise checkpoints every ~sqrt(3 nt) steps.
  * Gradients are identical either way. */
 int fwi_set_checkpoint(int every);
+
+/* Length of the FP32 accumulation chunks of the gradient (no counterpart in the paper; the
+ * time integral of the zero-lag cross-correlation of Sec. "Modelling and Inversion" is a sum
+ * over all steps).  steps > 0: plans made afterwards flush the FP32 per-shot accumulators
+ * into the FP64 sums after every `steps` adjoint steps (and after the last); 0 restores the
+ * default of 64.  A value of at least nt keeps one FP32 sum over the whole record.  Returns
+ * FWI_EINVAL for steps < 0. */
+int fwi_set_accumulation(int steps);
 
 /* Launch-shape tuning (no counterpart in the paper: the tile-shape autotuner's hook).  By
  * default the strip height of the streaming kernels is tuned online: for each launch shape

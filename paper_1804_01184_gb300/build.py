@@ -17,8 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfwi.so")
 SOURCES = [os.path.join(CSRC, "fwi_api.cu"), os.path.join(CSRC, "fwi_noalloc.cu")]
-DEPS = SOURCES + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".cu", ".h"))) + \
-    [os.path.join(ROOT, "include", "fwi.h")]
+# every file the translation units include: a change to any of them rebuilds the library
+DEP_SUFFIXES = (".cuh", ".cu", ".h", ".inc")
+DEPS = SOURCES + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(DEP_SUFFIXES)) + \
+    sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -90,6 +90,10 @@ int g_tile_tz = 0;
 int g_tile_variant = 0;
 // Checkpoint interval forced by fwi_set_checkpoint (0: the planner chooses).
 int g_ckpt_every = 0;
+// Adjoint steps whose gradient products accumulate in FP32 before they are flushed into the
+// FP64 running sums (fwi_set_accumulation; 0: ACC_STEPS).
+constexpr int ACC_STEPS = 64;
+int g_acc_every = 0;
 
 constexpr size_t ALIGN = 256;
 constexpr int RED_BLOCKS = 264;   // misfit partial sums per shot group
@@ -106,6 +110,8 @@ struct Plan {
     int ngroups = 0;
     int tz = 0;       // rows per warp strip
     int variant = 0;  // kernel variant (register budget) chosen by the tuner
+    int acc = ACC_STEPS;   // adjoint steps per FP32 accumulation chunk
+    bool rows = false;     // receiver-row table laid out (adjoint and gradient plans)
     // byte offsets into the workspace
     size_t status = 0, K = 0, bx = 0, bz = 0, ax = 0, axh = 0, az = 0, azh = 0;
     size_t sidx = 0, sw = 0, ridx = 0, rw = 0, rl = 0;
@@ -113,7 +119,8 @@ struct Plan {
     size_t dK = 0, dbx = 0, dbz = 0, dp[2] = {0, 0}, dvx[2] = {0, 0}, dvz[2] = {0, 0};
     size_t ap[2] = {0, 0}, avx[2] = {0, 0}, avz[2] = {0, 0};
     size_t accK = 0, accBx = 0, accBz = 0, snap = 0, ckpt = 0;
-    size_t gK = 0, hx = 0, hz = 0, traces = 0, partial = 0;
+    size_t gK = 0, hx = 0, hz = 0, traces = 0, partial = 0;   // gK, hx, hz: FP64 running sums
+    size_t rrow = 0, rcur = 0, rcell = 0;
     size_t total = 0;
 };
 
@@ -145,6 +152,7 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
     P.ns = ns; P.nr = nr; P.nt = g->nt;
     P.tz = g_tile_tz;   // 0: chosen per launch by strip_height()
     P.variant = g_tile_variant;
+    P.acc = g_acc_every > 0 ? g_acc_every : ACC_STEPS;
     P.B = std::max(1, std::min(B, std::max(ns, 1)));
     P.C = std::max(1, std::min(C, g->nt));
     P.nseg = (g->nt + P.C - 1) / P.C;
@@ -173,6 +181,10 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
         P.snap = take((size_t)(P.C + 1) * bfield);
         if (P.nseg > 1) P.ckpt = take((size_t)P.nseg * 3 * bfield);
         P.gK = take((size_t)d.Np * D); P.hx = take((size_t)d.Np * D); P.hz = take((size_t)d.Np * D);
+        P.rows = true;
+        P.rrow = take((size_t)(d.Nz + 1) * sizeof(int));
+        P.rcur = take((size_t)d.Nz * sizeof(int));
+        P.rcell = take(4 * (size_t)std::max(nr, 1) * sizeof(int2));
     }
     if (op == FWI_OP_GRADIENT) {
         P.traces = take((size_t)P.B * std::max(nr, 1) * g->nt * F);
@@ -302,6 +314,9 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
                at<long long>(work, P.ridx), at<float>(work, P.rw), status);
         LAUNCH(fwi::k_receiver_chain, (4 * rec->nr + 127) / 128, 128, 0, st, at<long long>(work, P.ridx), 4 * rec->nr,
                at<int>(work, P.rl));
+        if (P.rows)
+            LAUNCH(fwi::k_receiver_rows, 1, fwi::ROWS_THREADS, 0, st, at<long long>(work, P.ridx), at<int>(work, P.rl),
+                   4 * rec->nr, d.Px, d.Nz, at<int>(work, P.rrow), at<int>(work, P.rcur), at<int2>(work, P.rcell));
     }
     return FWI_OK;
 }
@@ -663,8 +678,32 @@ int forward_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
     return FWI_OK;
 }
 
+// FP32 accumulators of the group's bg slots into the FP64 running sums, slots cleared.
+void flush_acc(const Plan &P, void *work, int bg, cudaStream_t st)
+{
+    const long long units = P.d.Np / 4;
+    LAUNCH(fwi::k_acc_flush, (unsigned)((units + 255) / 256), 256, 0, st, at<float>(work, P.accK),
+           at<float>(work, P.accBx), at<float>(work, P.accBz), bg, P.d.Np, at<double>(work, P.gK),
+           at<double>(work, P.hx), at<double>(work, P.hz));
+}
+
+// Adjoint step n of a group (one launch): pbar^{n+1}, vbar^{n+1/2} -> pbar^n, vbar^{n-1/2},
+// the gradient products into the FP32 accumulators, and the receiver injection of r_{n-1}
+// into pbar^n.  pn: p^n of the group's shots.  Shared by the single calls and the engine.
+fwi::AdjArgs adj_args(const Plan &P, void *work, int n, int bg, const float *pn, const float *res)
+{
+    const int i = (n + 1) & 1, o = n & 1;
+    return fwi::AdjArgs{at<float>(work, P.ap[i]), at<float>(work, P.avx[i]), at<float>(work, P.avz[i]),
+                        at<float>(work, P.ap[o]), at<float>(work, P.avx[o]), at<float>(work, P.avz[o]),
+                        model_of(P, work), pn, at<float>(work, P.accK), at<float>(work, P.accBx),
+                        at<float>(work, P.accBz), res, at<int>(work, P.rrow), at<int2>(work, P.rcell),
+                        at<float>(work, P.rw), at<int>(work, P.rl), P.d, P.st, P.tz, bg, P.nr, P.nt,
+                        (P.nr > 0 && res && n >= 1) ? n - 1 : -1};
+}
+
 // Adjoint over all segments for one group (history from forward_group), accumulating into
-// the per-slot FP32 accumulators.  res: [bg][nr][nt] residual of the group.
+// the per-slot FP32 accumulators and, every P.acc steps and after step 0, into the FP64
+// running sums.  res: [bg][nr][nt] residual of the group.
 int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, int s0, int bg,
                   const float *res)
 {
@@ -676,9 +715,13 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
     CK(cudaMemsetAsync(at<char>(work, P.ap[first]), 0, bf, st));
     CK(cudaMemsetAsync(at<char>(work, P.avx[first]), 0, bf, st));
     CK(cudaMemsetAsync(at<char>(work, P.avz[first]), 0, bf, st));
-    const fwi::Model mo = model_of(P, work);
-    float *aK = at<float>(work, P.accK), *aBx = at<float>(work, P.accBx), *aBz = at<float>(work, P.accBz);
     float *snap = at<float>(work, P.snap);
+    if (P.nr > 0 && P.nt > 0) {   // r_{nt-1} into pbar^{nt}, with its K-gradient term (R^T r) p^{nt}
+        const float *pend = snap + (size_t)(P.nt - (P.nseg - 1) * P.C) * slot;
+        LAUNCH(fwi::k_adj_inject_k, (bg * 4 * P.nr + 127) / 128, 128, 0, st, at<float>(work, P.ap[first]),
+               at<float>(work, P.accK), pend, bg, P.nr, P.nt, P.nt - 1, d.Np, at<long long>(work, P.ridx),
+               at<float>(work, P.rw), at<int>(work, P.rl), res);
+    }
     for (int k = P.nseg - 1; k >= 0; --k) {
         const int n0 = k * P.C, n1 = std::min(n0 + P.C, P.nt);
         if (k < P.nseg - 1) {   // recompute the segment from its checkpoint
@@ -690,39 +733,40 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
                 f.step(n, s0, bg, snap + (size_t)(n - n0) * slot, snap + (size_t)(n + 1 - n0) * slot);
         }
         for (int n = n1 - 1; n >= n0; --n) {
-            const int i = (n + 1) & 1, o = n & 1;
-            float *ap0 = at<float>(work, P.ap[i]);
-            const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
-            if (P.nr > 0)
-                LAUNCH(fwi::k_adj_inject_k, (bg * 4 * P.nr + 127) / 128, 128, 0, st, ap0, aK, pn1, bg, P.nr, P.nt, n,
-                       d.Np, at<long long>(work, P.ridx), at<float>(work, P.rw), at<int>(work, P.rl), res);
-            const float *avx0 = at<float>(work, P.avx[i]), *avz0 = at<float>(work, P.avz[i]);
-            float *ap1 = at<float>(work, P.ap[o]), *avx1 = at<float>(work, P.avx[o]), *avz1 = at<float>(work, P.avz[o]);
             const size_t S = P.M == 2 ? fwi::adj_smem<2>() : fwi::adj_smem<4>();
             const void *K0 = P.M == 2 ? (const void *)fwi::k_adj_warp<2, 1> : (const void *)fwi::k_adj_warp<4, 1>;
             StripTuner::Key key;
             StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, 32, S), st, key);
-            const int tz = ts.tz;
-            const dim3 grid = warp_grid(P, tz, bg, 1);
-#define ADJ_ARGS fwi::AdjArgs{ap0, avx0, avz0, ap1, avx1, avz1, mo, pn, aK, aBx, aBz, d, P.st, tz, bg}
+            fwi::AdjArgs args = adj_args(P, work, n, bg, snap + (size_t)(n - n0) * slot, res);
+            args.tz = ts.tz;
+            const dim3 grid = warp_grid(P, ts.tz, bg, 1);
             constexpr int B128 = fwi::minb(128, 32), B170 = fwi::minb(170, 32);
             if (P.M == 2) {
                 switch (P.variant) {
-                case 1: SLAUNCH((fwi::k_adj_warp<2, B128>), grid, 32, S, st, ADJ_ARGS); break;
-                case 2: SLAUNCH((fwi::k_adj_warp<2, B170>), grid, 32, S, st, ADJ_ARGS); break;
-                default: SLAUNCH((fwi::k_adj_warp<2, 1>), grid, 32, S, st, ADJ_ARGS);
+                case 1: SLAUNCH((fwi::k_adj_warp<2, B128>), grid, 32, S, st, args); break;
+                case 2: SLAUNCH((fwi::k_adj_warp<2, B170>), grid, 32, S, st, args); break;
+                default: SLAUNCH((fwi::k_adj_warp<2, 1>), grid, 32, S, st, args);
                 }
             } else {
                 switch (P.variant) {
-                case 1: SLAUNCH((fwi::k_adj_warp<4, B128>), grid, 32, S, st, ADJ_ARGS); break;
-                case 2: SLAUNCH((fwi::k_adj_warp<4, B170>), grid, 32, S, st, ADJ_ARGS); break;
-                default: SLAUNCH((fwi::k_adj_warp<4, 1>), grid, 32, S, st, ADJ_ARGS);
+                case 1: SLAUNCH((fwi::k_adj_warp<4, B128>), grid, 32, S, st, args); break;
+                case 2: SLAUNCH((fwi::k_adj_warp<4, B170>), grid, 32, S, st, args); break;
+                default: SLAUNCH((fwi::k_adj_warp<4, 1>), grid, 32, S, st, args);
                 }
             }
             g_tuner.finish(key, ts, st);
-#undef ADJ_ARGS
+            if (n % P.acc == 0) flush_acc(P, work, bg, st);
         }
     }
+    return FWI_OK;
+}
+
+// Zeroes the FP32 slot accumulators and the FP64 running sums of a gradient plan.
+int clear_acc(const Plan &P, void *work, cudaStream_t st)
+{
+    const size_t bf = (size_t)P.B * P.d.Np * sizeof(float), bd = (size_t)P.d.Np * sizeof(double);
+    for (size_t o : {P.accK, P.accBx, P.accBz}) CK(cudaMemsetAsync(at<char>(work, o), 0, bf, st));
+    for (size_t o : {P.gK, P.hx, P.hz}) CK(cudaMemsetAsync(at<char>(work, o), 0, bd, st));
     return FWI_OK;
 }
 
@@ -731,8 +775,7 @@ int finalize_grad(const Plan &P, const fwi_grid *g, int pz, const float *xa, con
 {
     const fwi::Dims &d = P.d;
     dim3 b2(32, 8), gp((d.Nx + 31) / 32, (d.Nz + 7) / 8), gq((d.nx + 31) / 32, (d.nz + 7) / 8);
-    LAUNCH(fwi::k_grad_cells, gp, b2, 0, st, at<float>(work, P.accK), at<float>(work, P.accBx),
-           at<float>(work, P.accBz), P.B, at<float>(work, P.K), at<float>(work, P.bx), at<float>(work, P.bz), d,
+    LAUNCH(fwi::k_grad_cells, gp, b2, 0, st, at<float>(work, P.K), at<float>(work, P.bx), at<float>(work, P.bz), d,
            at<double>(work, P.gK), at<double>(work, P.hx), at<double>(work, P.hz));
     LAUNCH(fwi::k_grad_final, gq, b2, 0, st, at<double>(work, P.gK), at<double>(work, P.hx),
            at<double>(work, P.hz), xa, xb, pz, g->vp_o, g->rho_o, d, grads);
@@ -748,10 +791,7 @@ int adjoint_impl(const fwi_grid *g, int pz, const float *xa, const float *xb, co
     int rc = plan_for(P, g, op, src->ns, rec->nr, work_bytes);
     if (rc) return rc;
     if ((rc = setup(P, g, pz, xa, xb, src, rec, work, st))) return rc;
-    const size_t bf = (size_t)P.B * P.d.Np * sizeof(float);
-    CK(cudaMemsetAsync(at<char>(work, P.accK), 0, bf, st));
-    CK(cudaMemsetAsync(at<char>(work, P.accBx), 0, bf, st));
-    CK(cudaMemsetAsync(at<char>(work, P.accBz), 0, bf, st));
+    if ((rc = clear_acc(P, work, st))) return rc;
     const long long per_shot = (long long)P.nr * P.nt;
     for (int gi = 0; gi < P.ngroups; ++gi) {
         const int s0 = gi * P.B, bg = std::min(P.B, P.ns - s0);
@@ -937,7 +977,6 @@ int fwi_status(void *work, void *stream)
     CK(cudaStreamSynchronize(st));
     if (h & fwi::ST_EINVAL) return fail(FWI_EINVAL, "a contrast has 1 + xi <= 0 or a position lies outside the physical grid");
     if (h & fwi::ST_ECFL) return fail(FWI_ECFL, "dt exceeds the stability limit of the stencil for this model");
-    if (h & fwi::ST_ETIMEOUT) return fail(FWI_ETIMEOUT, "a bounded wait for a TMA row copy expired");
     return FWI_OK;
 }
 
@@ -966,6 +1005,13 @@ int fwi_set_checkpoint(int every)
 {
     if (every < 0) return fail(FWI_EINVAL, "checkpoint interval must be >= 0");
     g_ckpt_every = every;
+    return FWI_OK;
+}
+
+int fwi_set_accumulation(int steps)
+{
+    if (steps < 0) return fail(FWI_EINVAL, "accumulation chunk must be >= 0 steps");
+    g_acc_every = steps;
     return FWI_OK;
 }
 

@@ -194,6 +194,47 @@ __global__ void k_receiver_chain(const long long *__restrict__ idx, int n4, int 
     rl[k] = nx | (first ? CHAIN_FIRST : 0);
 }
 
+// Unique receiver cells (the first footprint entry of each cell's chain) listed by padded row,
+// for the adjoint launches that inject the residual while they write each row:
+// rrow[j] .. rrow[j+1] index the cells of row j in rcell, each (column, first entry).  One
+// block; rcur (Nz ints) is its scratch.  The order of the cells within a row is free: each
+// cell is a different address, injected by the one lane that owns it.
+constexpr int ROWS_THREADS = 1024;
+
+__global__ void __launch_bounds__(ROWS_THREADS) k_receiver_rows(const long long *__restrict__ idx,
+                                                                const int *__restrict__ rl, int n4, int Px, int Nz,
+                                                                int *__restrict__ rrow, int *__restrict__ rcur,
+                                                                int2 *__restrict__ rcell)
+{
+    __shared__ int part[ROWS_THREADS];
+    const int t = threadIdx.x;
+    for (int j = t; j < Nz; j += ROWS_THREADS) rcur[j] = 0;
+    __syncthreads();
+    for (int k = t; k < n4; k += ROWS_THREADS)
+        if (rl[k] & CHAIN_FIRST) atomicAdd(&rcur[(int)(idx[k] / Px)], 1);
+    __syncthreads();
+    // exclusive scan of the row counts: thread t takes rows [t*per, (t+1)*per)
+    const int per = (Nz + ROWS_THREADS - 1) / ROWS_THREADS, lo = min(t * per, Nz), hi = min(lo + per, Nz);
+    int own = 0;
+    for (int j = lo; j < hi; ++j) own += rcur[j];
+    part[t] = own;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int k = 0; k < ROWS_THREADS; ++k) { const int c = part[k]; part[k] = run; run += c; }
+        rrow[Nz] = run;
+    }
+    __syncthreads();
+    int run = part[t];
+    for (int j = lo; j < hi; ++j) { const int c = rcur[j]; rrow[j] = run; rcur[j] = run; run += c; }
+    __syncthreads();
+    for (int k = t; k < n4; k += ROWS_THREADS)
+        if (rl[k] & CHAIN_FIRST) {
+            const int j = (int)(idx[k] / Px), i = (int)(idx[k] - (long long)j * Px);
+            rcell[atomicAdd(&rcur[j], 1)] = make_int2(i, k);
+        }
+}
+
 // ------------------------------------------------------------ shared kernel arguments
 
 struct Model {
@@ -299,26 +340,49 @@ __global__ void __launch_bounds__(RED_THREADS) k_sum_final(const double *__restr
     if (threadIdx.x == 0) out[0] = acc;
 }
 
-// Per padded cell, FP64: gK = sum_s accK / K;  hx = g_bx * d bx/d rho_each = (sum_s accBx) bx^2/2
-// (g_bx = -sum accBx, d bx / d rho = -bx^2/2 for each of its two cells), hz likewise.
-__global__ void k_grad_cells(const float *__restrict__ accK, const float *__restrict__ accBx,
-                             const float *__restrict__ accBz, int nslots, const float *__restrict__ K,
-                             const float *__restrict__ bx, const float *__restrict__ bz, Dims d,
-                             double *__restrict__ gK, double *__restrict__ hx, double *__restrict__ hz)
+// Gradient accumulation in time: every adjoint launch adds one step's zero-lag products to
+// FP32 per-shot-slot fields (one red per address per launch, so the order is fixed); after a
+// chunk of steps the slots are flushed into FP64 running sums over shots and cleared.  Thread
+// t takes the float4 of cells 4t .. 4t+3 of every slot (Np is a multiple of 32): the slots are
+// summed in FP64 in slot order and the sum is added to the running sum.
+__global__ void k_acc_flush(float *__restrict__ accK, float *__restrict__ accBx, float *__restrict__ accBz,
+                            int nslots, long long Np, double *__restrict__ sK, double *__restrict__ sX,
+                            double *__restrict__ sZ)
+{
+    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e >= Np) return;
+    float *acc[3] = {accK, accBx, accBz};
+    double *sum[3] = {sK, sX, sZ};
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int s = 0; s < nslots; ++s) {
+            float4 *q = reinterpret_cast<float4 *>(acc[f] + s * Np + e);
+            const float4 v = *q;
+            a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+            *q = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        double2 *o = reinterpret_cast<double2 *>(sum[f] + e);
+        const double2 lo = o[0], hi = o[1];
+        o[0] = make_double2(lo.x + a0, lo.y + a1);
+        o[1] = make_double2(hi.x + a2, hi.y + a3);
+    }
+}
+
+// Per padded cell, FP64, in place on the running sums of k_acc_flush:
+// gK = sum accK / K;  hx = g_bx * d bx/d rho_each = (sum accBx) bx^2/2 (g_bx = -sum accBx,
+// d bx / d rho = -bx^2/2 for each of its two cells), hz likewise.
+__global__ void k_grad_cells(const float *__restrict__ K, const float *__restrict__ bx,
+                             const float *__restrict__ bz, Dims d, double *__restrict__ gK,
+                             double *__restrict__ hx, double *__restrict__ hz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= d.Nx || j >= d.Nz) return;
     const long long m = cell(d, i, j);
-    double sK = 0.0, sx = 0.0, sz = 0.0;
-    for (int s = 0; s < nslots; ++s) {
-        sK += accK[s * d.Np + m];
-        sx += accBx[s * d.Np + m];
-        sz += accBz[s * d.Np + m];
-    }
     const double b1 = bx[m], b2 = bz[m];
-    gK[m] = sK / (double)K[m];
-    hx[m] = 0.5 * b1 * b1 * sx;
-    hz[m] = 0.5 * b2 * b2 * sz;
+    gK[m] = gK[m] / (double)K[m];
+    hx[m] = 0.5 * b1 * b1 * hx[m];
+    hz[m] = 0.5 * b2 * b2 * hz[m];
 }
 
 // Per physical cell: fold the padding it feeds, form g_rho from the buoyancy nodes that

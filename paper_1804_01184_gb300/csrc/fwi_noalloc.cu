@@ -79,3 +79,24 @@ extern "C" int fwi_model_noalloc(const fwi_grid *g, fwi_param pz, const float *x
     // whatever the previous call left in the scratch does not matter.
     return fwi_model(g, pz, xi_a, xi_b, src, rec, traces, scratch, (size_t)FWI_NOALLOC_SCRATCH_BYTES, stream);
 }
+
+// The status word fwi_model_noalloc's kernels record lives at the start of the built-in
+// scratch of the current device; fwi_status reads and clears it there.  Before any call on
+// this device there is nothing to report.
+extern "C" int fwi_status_noalloc(void *stream)
+{
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "fwi_status_noalloc: no usable current device (%s)", cudaGetErrorString(e));
+        fwi_internal::set_error(msg);
+        return FWI_ECUDA;
+    }
+    void *scratch;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        scratch = g_addr[dev];
+    }
+    return scratch ? fwi_status(scratch, stream) : FWI_OK;
+}

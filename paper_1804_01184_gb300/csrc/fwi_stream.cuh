@@ -5,11 +5,13 @@
 // shared memory with a 4-column zero halo (SHALO) on each side.
 #pragma once
 #include "fwi_kernels.cuh"
-#include "fwi_tma.cuh"
 
 namespace fwi {
 
 constexpr int SHALO = 4;   // zero columns on each side of a shared row (one float4)
+
+// shared-memory address of a generic pointer into shared memory (for cp.async)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ float4 f4(float v) { return make_float4(v, v, v, v); }
 

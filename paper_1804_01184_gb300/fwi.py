@@ -4,7 +4,8 @@ Argument marshalling only: every step of the method runs in the library's CUDA k
 PyTorch supplies device memory (inputs, outputs and the scratch workspace) and streams.
 The functions carry the C names: ``fwi_model``, ``fwi_born``, ``fwi_adjoint``,
 ``fwi_gradient`` (optionally weighted per trace), ``fwi_misfit``, ``fwi_workspace_bytes``,
-``fwi_status``, ``fwi_model_noalloc``, ``fwi_set_tile``, ``fwi_set_checkpoint``.
+``fwi_status``, ``fwi_model_noalloc``, ``fwi_status_noalloc``, ``fwi_set_tile``, ``fwi_set_checkpoint``,
+``fwi_set_accumulation``.
 
 There is no fallback: if libfwi.so has not been built (``paper_1804_01184_gb300.build``)
 or no CUDA device is present, these functions raise.
@@ -83,7 +84,9 @@ def lib():
             L.fwi_launch_count.restype = C.c_longlong
             L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
             L.fwi_set_checkpoint.argtypes = [C.c_int]
+            L.fwi_set_accumulation.argtypes = [C.c_int]
             L.fwi_model_noalloc.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp]
+            L.fwi_status_noalloc.argtypes = [vp]
             L.fwi_profile.argtypes = [C.c_int]
             L.fwi_profile_report.argtypes = [C.c_char_p, C.c_size_t]
             _lib = L
@@ -111,6 +114,28 @@ def _dev(t, dtype=torch.float32):
 def _stream(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
+
+
+class _OnStream:
+    """Orders a library call on a caller-given stream after the current stream (where the
+    binding converted and copied the inputs) and, after the call, ties every tensor the call
+    reads or writes to that stream, so the caching allocator does not reuse their memory
+    before the library's kernels are done with it.  No-op for the current stream."""
+
+    def __init__(self, stream):
+        cur = torch.cuda.current_stream()
+        self.stream = stream if stream is not None and stream != cur else None
+        if self.stream is not None:
+            self.stream.wait_stream(cur)
+
+    def keep(self, *tensors):
+        if self.stream is None:
+            return
+        for t in tensors:
+            if isinstance(t, (tuple, list)):
+                self.keep(*t)
+            elif torch.is_tensor(t) and t.is_cuda:
+                t.record_stream(self.stream)
 
 
 def fwi_workspace_bytes(grid: Grid, ns: int, nr: int, op: int, budget_bytes: int = 0) -> int:
@@ -147,6 +172,11 @@ def fwi_set_checkpoint(every: int = 0):
     _raise(lib().fwi_set_checkpoint(int(every)))
 
 
+def fwi_set_accumulation(steps: int = 0):
+    """Adjoint steps per FP32 gradient-accumulation chunk for plans made afterwards (0 = 64)."""
+    _raise(lib().fwi_set_accumulation(int(steps)))
+
+
 def launch_count() -> int:
     return int(lib().fwi_launch_count())
 
@@ -165,24 +195,37 @@ def fwi_model(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, traces=N
         traces = torch.empty((S.ns, R.nr, grid.nt), dtype=torch.float32, device="cuda")
     if work is None:
         work = workspace(grid, S.ns, R.nr, OP_MODEL)
+    on = _OnStream(stream)
     _raise(lib().fwi_model(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(traces),
                            _ptr(work), work.numel(), _stream(stream)))
+    on.keep(a, b, keep, traces, work)
     if check:
         fwi_status(work, stream)
     return traces
 
 
 def fwi_model_noalloc(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, traces=None,
-                      stream=None) -> torch.Tensor:
+                      stream=None, check=True) -> torch.Tensor:
     """fwi_model on the library's built-in scratch, for callers that cannot allocate device
-    memory (see fwi_model_noalloc in include/fwi.h: size limit, first-call set-up, sharing)."""
+    memory (see fwi_model_noalloc in include/fwi.h: size limit, first-call set-up, sharing).
+    check: wait for the stream and raise the data-dependent errors the call recorded
+    (fwi_status_noalloc)."""
     a, b = _dev(xi_a), _dev(xi_b)
     keep, S, R = _acq(src_xy, wavelet, rec_xy)
     if traces is None:
         traces = torch.empty((S.ns, R.nr, grid.nt), dtype=torch.float32, device="cuda")
+    on = _OnStream(stream)
     _raise(lib().fwi_model_noalloc(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R),
                                    _ptr(traces), _stream(stream)))
+    on.keep(a, b, keep, traces)
+    if check:
+        fwi_status_noalloc(stream)
     return traces
+
+
+def fwi_status_noalloc(stream=None):
+    """Raises the data-dependent error the last fwi_model_noalloc call on this device recorded."""
+    _raise(lib().fwi_status_noalloc(_stream(stream)))
 
 
 def fwi_born(grid: Grid, pz: int, xi_a, xi_b, dxi_a, dxi_b, src_xy, wavelet, rec_xy, dtraces=None,
@@ -194,8 +237,10 @@ def fwi_born(grid: Grid, pz: int, xi_a, xi_b, dxi_a, dxi_b, src_xy, wavelet, rec
         dtraces = torch.empty((S.ns, R.nr, grid.nt), dtype=torch.float32, device="cuda")
     if work is None:
         work = workspace(grid, S.ns, R.nr, OP_BORN)
+    on = _OnStream(stream)
     _raise(lib().fwi_born(C.byref(grid), int(pz), _ptr(a), _ptr(b), _ptr(da), _ptr(db), C.byref(S),
                           C.byref(R), _ptr(dtraces), _ptr(work), work.numel(), _stream(stream)))
+    on.keep(a, b, da, db, keep, dtraces, work)
     if check:
         fwi_status(work, stream)
     return dtraces
@@ -210,8 +255,10 @@ def fwi_adjoint(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, residu
         grads = torch.empty((5, 2, grid.nz, grid.nx), dtype=torch.float64, device="cuda")
     if work is None:
         work = workspace(grid, S.ns, R.nr, OP_ADJOINT)
+    on = _OnStream(stream)
     _raise(lib().fwi_adjoint(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(res),
                              _ptr(grads), _ptr(work), work.numel(), _stream(stream)))
+    on.keep(a, b, res, keep, grads, work)
     if check:
         fwi_status(work, stream)
     return grads
@@ -229,16 +276,18 @@ def fwi_gradient(grid: Grid, pz: int, xi_a, xi_b, src_xy, wavelet, rec_xy, data,
         misfit = torch.empty((), dtype=torch.float64, device="cuda")
     if work is None:
         work = workspace(grid, S.ns, R.nr, OP_GRADIENT)
-    if weights is None:
+    wt = _dev(weights) if weights is not None else None
+    if wt is not None and wt.numel() != S.ns * R.nr:
+        raise FwiError(-1, "weights must hold ns x nr values")
+    on = _OnStream(stream)
+    if wt is None:
         _raise(lib().fwi_gradient(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R), _ptr(d),
                                   _ptr(misfit), _ptr(grads), _ptr(work), work.numel(), _stream(stream)))
     else:
-        wt = _dev(weights)
-        if wt.numel() != S.ns * R.nr:
-            raise FwiError(-1, "weights must hold ns x nr values")
         _raise(lib().fwi_gradient_weighted(C.byref(grid), int(pz), _ptr(a), _ptr(b), C.byref(S), C.byref(R),
                                            _ptr(d), _ptr(wt), _ptr(misfit), _ptr(grads), _ptr(work), work.numel(),
                                            _stream(stream)))
+    on.keep(a, b, d, wt, keep, misfit, grads, work)
     if check:
         fwi_status(work, stream)
     return misfit, grads
@@ -252,12 +301,14 @@ def fwi_misfit(traces, data, misfit=None, stream=None, weights=None, nt=None) ->
         raise FwiError(-1, "traces and data differ in size")
     if misfit is None:
         misfit = torch.empty((), dtype=torch.float64, device="cuda")
-    if weights is None:
+    wt = _dev(weights) if weights is not None else None
+    if wt is not None and (nt is None or wt.numel() * nt != t.numel()):
+        raise FwiError(-1, "weights x nt must cover the traces")
+    on = _OnStream(stream)
+    if wt is None:
         _raise(lib().fwi_misfit(_ptr(t), _ptr(d), t.numel(), _ptr(misfit), _stream(stream)))
     else:
-        wt = _dev(weights)
-        if nt is None or wt.numel() * nt != t.numel():
-            raise FwiError(-1, "weights x nt must cover the traces")
         _raise(lib().fwi_misfit_weighted(_ptr(t), _ptr(d), wt.numel(), int(nt), _ptr(wt), _ptr(misfit),
                                          _stream(stream)))
+    on.keep(t, d, wt, misfit)
     return misfit

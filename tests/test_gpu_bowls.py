@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1804_01184_gb300 import inputs as I
-from tests._common import TRACE_TOL, gpu_grid, oracle_grid
+from tests._common import GRAD_TOL, TRACE_TOL, gpu_grid, oracle_grid, rel_l2
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -82,3 +82,31 @@ def test_weighted_gradient_is_the_adjoint_of_the_masked_residual(L):
     J1, G1 = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data, weights=np.ones_like(wt))
     J0, G0 = F.fwi_gradient(g, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data)
     assert torch.equal(G1, G0) and J1.item() == J0.item()
+
+
+@pytest.mark.parametrize("lo,hi", [(0.0, 90.0), (135.0, 180.0)])
+def test_weighted_gradient_matches_the_oracle(L, lo, hi):
+    """Limited aperture (Sec. "Hierarchical Inversion"): fwi_gradient_weighted with the 0/1
+    weights of a scattering-angle range against the oracle -- the gradient is oracle.adjoint
+    of the masked residual w (oracle.model - data), the misfit 1/2 sum w (oracle.model -
+    data)^2 -- at the gradient and trace tolerances, for every field of all five
+    parameterizations."""
+    F, B = L
+    w = I.small_case(seed=34, nx=52, nz=48, nt=180, order=8, sponge=6, ns=4, nr=16, pz=I.PZ_VP_RHO)
+    c = I.centre_of(w.nx, w.nz, w.dx)
+    w.src_xy, w.rec_xy = I.circle(w.ns, 95.0, c), I.circle(w.nr, 95.0, c, 0.5)
+    wt = B.aperture_weights(w.src_xy, w.rec_xy, c, lo, hi)
+    assert 0 < wt.sum() < wt.size
+    og = oracle_grid(w)
+    data = oracle.model(og, w.pz, w.xi_a * 1.4, w.xi_b * 0.6, w.src_xy, w.wavelet, w.rec_xy).astype(np.float32)
+    a0, b0 = (w.xi_a * 0.5).astype(np.float32), (w.xi_b * 0.5).astype(np.float32)
+    d_mod = oracle.model(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy)
+    r = d_mod - data.astype(np.float64)
+    G_ref = oracle.adjoint(og, w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, wt[:, :, None] * r)
+    J_ref = 0.5 * float(np.sum(wt[:, :, None] * r * r))
+    J, G = F.fwi_gradient(gpu_grid(w), w.pz, a0, b0, w.src_xy, w.wavelet, w.rec_xy, data, weights=wt)
+    G = G.cpu().numpy()
+    assert abs(J.item() - J_ref) <= TRACE_TOL * J_ref
+    for pz in range(5):
+        for k in range(2):
+            assert rel_l2(G[pz, k], G_ref[pz, k]) <= GRAD_TOL, (pz, k, rel_l2(G[pz, k], G_ref[pz, k]))

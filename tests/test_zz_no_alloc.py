@@ -2,8 +2,11 @@
 (a service whose device memory is fixed at start-up, a plugin inside a framework that owns
 all device memory, code where an allocation may block).  It runs on the library's built-in
 scratch array instead of a caller workspace.  Two calls in a row, with different models,
-must match the existing entry point fwi_model on a caller workspace; a problem too large for
-the built-in scratch must be refused with FWI_ENOMEM.  This file is collected last."""
+must match the existing entry point fwi_model on a caller workspace -- bitwise, since both
+run the same kernels on the same plan shape and shot grouping does not change a shot's
+arithmetic; a problem too large for the built-in scratch must be refused with FWI_ENOMEM; a
+bad contrast recorded in the scratch must be reported by fwi_status_noalloc.  This file is
+collected last."""
 import numpy as np
 import pytest
 
@@ -35,6 +38,7 @@ def test_noalloc_matches_fwi_model_on_two_calls(F):
         torch.cuda.synchronize()
         out = out.cpu().numpy()
         assert np.all(np.isfinite(out))
+        np.testing.assert_array_equal(out, ref)
         assert rel_l2(out, ref) <= TRACE_TOL
 
 
@@ -49,3 +53,24 @@ def test_noalloc_refuses_problems_beyond_its_scratch(F):
     with pytest.raises(F.FwiError) as e:
         F.fwi_model_noalloc(g, 0, xa, xa, xy, wav, xy)
     assert e.value.code == -3 and "built-in scratch" in str(e.value)
+
+
+def test_noalloc_reports_a_bad_contrast(F):
+    """A contrast with 1 + xi <= 0 is a data-dependent error: the kernels record it in the
+    built-in scratch, fwi_status_noalloc returns FWI_EINVAL and clears it, and the next good
+    call reports nothing."""
+    from paper_1804_01184_gb300 import inputs as I
+    w = I.small_case(seed=90, nx=40, nz=36, nt=60, ns=2, nr=3)
+    g = F.make_grid(**w.grid_kwargs())
+    bad = w.xi_a.copy()
+    bad[5, 7] = -1.0
+    F.fwi_model_noalloc(g, w.pz, bad, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, check=False)
+    with pytest.raises(F.FwiError) as e:
+        F.fwi_status_noalloc()
+    assert e.value.code == -1
+    F.fwi_status_noalloc()                     # cleared
+    with pytest.raises(F.FwiError) as e:       # check=True raises it directly
+        F.fwi_model_noalloc(g, w.pz, bad, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    assert e.value.code == -1
+    out = F.fwi_model_noalloc(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+    assert torch.isfinite(out).all()
