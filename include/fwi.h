@@ -115,9 +115,11 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
  * (Sec. "Modelling and Inversion": gradient by adjoint modelling, then the chain rule).
  * Accumulation: each adjoint step's products go into FP32 per-shot fields; after every
  * chunk of steps (64 by default, fwi_set_accumulation) and after the last step those fields
- * are flushed into FP64 running sums over shots (a fixed order: results are bitwise
- * reproducible) and cleared, so no FP32 sum spans more than one chunk.  The density chain
- * rule and the parameterization chain rules run in FP64. */
+ * are flushed into FP64 running sums over shots and cleared, so no FP32 sum spans more than
+ * one chunk.  The flush adds a chunk's per-shot values with a compensated (TwoSum) FP32 sum,
+ * exact to about twice FP32 precision, and adds that to the FP64 sum; its order is fixed, so
+ * results are bitwise reproducible.  The density chain rule and the parameterization chain
+ * rules run in FP64. */
 int fwi_adjoint(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi_b,
                 const fwi_sources *src, const fwi_receivers *rec, const float *residual,
                 double *grads, void *work, size_t work_bytes, void *stream);

@@ -111,7 +111,6 @@ struct Plan {
     int tz = 0;       // rows per warp strip
     int variant = 0;  // kernel variant (register budget) chosen by the tuner
     int acc = ACC_STEPS;   // adjoint steps per FP32 accumulation chunk
-    bool rows = false;     // receiver-row table laid out (adjoint and gradient plans)
     // byte offsets into the workspace
     size_t status = 0, K = 0, bx = 0, bz = 0, ax = 0, axh = 0, az = 0, azh = 0;
     size_t sidx = 0, sw = 0, ridx = 0, rw = 0, rl = 0;
@@ -120,7 +119,6 @@ struct Plan {
     size_t ap[2] = {0, 0}, avx[2] = {0, 0}, avz[2] = {0, 0};
     size_t accK = 0, accBx = 0, accBz = 0, snap = 0, ckpt = 0;
     size_t gK = 0, hx = 0, hz = 0, traces = 0, partial = 0;   // gK, hx, hz: FP64 running sums
-    size_t rrow = 0, rcur = 0, rcell = 0;
     size_t total = 0;
 };
 
@@ -181,10 +179,6 @@ void layout(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, int B, int C)
         P.snap = take((size_t)(P.C + 1) * bfield);
         if (P.nseg > 1) P.ckpt = take((size_t)P.nseg * 3 * bfield);
         P.gK = take((size_t)d.Np * D); P.hx = take((size_t)d.Np * D); P.hz = take((size_t)d.Np * D);
-        P.rows = true;
-        P.rrow = take((size_t)(d.Nz + 1) * sizeof(int));
-        P.rcur = take((size_t)d.Nz * sizeof(int));
-        P.rcell = take(4 * (size_t)std::max(nr, 1) * sizeof(int2));
     }
     if (op == FWI_OP_GRADIENT) {
         P.traces = take((size_t)P.B * std::max(nr, 1) * g->nt * F);
@@ -314,9 +308,6 @@ int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float
                at<long long>(work, P.ridx), at<float>(work, P.rw), status);
         LAUNCH(fwi::k_receiver_chain, (4 * rec->nr + 127) / 128, 128, 0, st, at<long long>(work, P.ridx), 4 * rec->nr,
                at<int>(work, P.rl));
-        if (P.rows)
-            LAUNCH(fwi::k_receiver_rows, 1, fwi::ROWS_THREADS, 0, st, at<long long>(work, P.ridx), at<int>(work, P.rl),
-                   4 * rec->nr, d.Px, d.Nz, at<int>(work, P.rrow), at<int>(work, P.rcur), at<int2>(work, P.rcell));
     }
     return FWI_OK;
 }
@@ -679,26 +670,27 @@ int forward_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
 }
 
 // FP32 accumulators of the group's bg slots into the FP64 running sums, slots cleared.
-void flush_acc(const Plan &P, void *work, int bg, cudaStream_t st)
+int flush_acc(const Plan &P, void *work, int bg, cudaStream_t st)
 {
     const long long units = P.d.Np / 4;
-    LAUNCH(fwi::k_acc_flush, (unsigned)((units + 255) / 256), 256, 0, st, at<float>(work, P.accK),
-           at<float>(work, P.accBx), at<float>(work, P.accBz), bg, P.d.Np, at<double>(work, P.gK),
-           at<double>(work, P.hx), at<double>(work, P.hz));
+    LAUNCH(fwi::k_acc_flush, dim3((unsigned)((units + fwi::FLUSH_X - 1) / fwi::FLUSH_X), 3),
+           dim3(fwi::FLUSH_X, fwi::FLUSH_Y), 0, st, at<float>(work, P.accK), at<float>(work, P.accBx),
+           at<float>(work, P.accBz), bg, P.d.Np, at<double>(work, P.gK), at<double>(work, P.hx), at<double>(work, P.hz));
+    const size_t bf = (size_t)bg * P.d.Np * sizeof(float);
+    for (size_t o : {P.accK, P.accBx, P.accBz}) CK(cudaMemsetAsync(at<char>(work, o), 0, bf, st));
+    return FWI_OK;
 }
 
-// Adjoint step n of a group (one launch): pbar^{n+1}, vbar^{n+1/2} -> pbar^n, vbar^{n-1/2},
-// the gradient products into the FP32 accumulators, and the receiver injection of r_{n-1}
-// into pbar^n.  pn: p^n of the group's shots.  Shared by the single calls and the engine.
-fwi::AdjArgs adj_args(const Plan &P, void *work, int n, int bg, const float *pn, const float *res)
+// Adjoint step n of a group (one launch): pbar^{n+1} (after its receiver injection),
+// vbar^{n+1/2} -> pbar^n, vbar^{n-1/2}, the gradient products into the FP32 accumulators.
+// pn: p^n of the group's shots.  Shared by the single calls and the engine.
+fwi::AdjArgs adj_args(const Plan &P, void *work, int n, int bg, const float *pn)
 {
     const int i = (n + 1) & 1, o = n & 1;
     return fwi::AdjArgs{at<float>(work, P.ap[i]), at<float>(work, P.avx[i]), at<float>(work, P.avz[i]),
                         at<float>(work, P.ap[o]), at<float>(work, P.avx[o]), at<float>(work, P.avz[o]),
                         model_of(P, work), pn, at<float>(work, P.accK), at<float>(work, P.accBx),
-                        at<float>(work, P.accBz), res, at<int>(work, P.rrow), at<int2>(work, P.rcell),
-                        at<float>(work, P.rw), at<int>(work, P.rl), P.d, P.st, P.tz, bg, P.nr, P.nt,
-                        (P.nr > 0 && res && n >= 1) ? n - 1 : -1};
+                        at<float>(work, P.accBz), P.d, P.st, P.tz, bg};
 }
 
 // Adjoint over all segments for one group (history from forward_group), accumulating into
@@ -716,12 +708,6 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
     CK(cudaMemsetAsync(at<char>(work, P.avx[first]), 0, bf, st));
     CK(cudaMemsetAsync(at<char>(work, P.avz[first]), 0, bf, st));
     float *snap = at<float>(work, P.snap);
-    if (P.nr > 0 && P.nt > 0) {   // r_{nt-1} into pbar^{nt}, with its K-gradient term (R^T r) p^{nt}
-        const float *pend = snap + (size_t)(P.nt - (P.nseg - 1) * P.C) * slot;
-        LAUNCH(fwi::k_adj_inject_k, (bg * 4 * P.nr + 127) / 128, 128, 0, st, at<float>(work, P.ap[first]),
-               at<float>(work, P.accK), pend, bg, P.nr, P.nt, P.nt - 1, d.Np, at<long long>(work, P.ridx),
-               at<float>(work, P.rw), at<int>(work, P.rl), res);
-    }
     for (int k = P.nseg - 1; k >= 0; --k) {
         const int n0 = k * P.C, n1 = std::min(n0 + P.C, P.nt);
         if (k < P.nseg - 1) {   // recompute the segment from its checkpoint
@@ -733,11 +719,16 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
                 f.step(n, s0, bg, snap + (size_t)(n - n0) * slot, snap + (size_t)(n + 1 - n0) * slot);
         }
         for (int n = n1 - 1; n >= n0; --n) {
+            const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
+            if (P.nr > 0)   // pbar^{n+1} += R^T r_n, with its K-gradient term (R^T r_n) p^{n+1}
+                LAUNCH(fwi::k_adj_inject_k, (bg * 4 * P.nr + 127) / 128, 128, 0, st, at<float>(work, P.ap[(n + 1) & 1]),
+                       at<float>(work, P.accK), pn1, bg, P.nr, P.nt, n, d.Np, at<long long>(work, P.ridx),
+                       at<float>(work, P.rw), at<int>(work, P.rl), res);
             const size_t S = P.M == 2 ? fwi::adj_smem<2>() : fwi::adj_smem<4>();
             const void *K0 = P.M == 2 ? (const void *)fwi::k_adj_warp<2, 1> : (const void *)fwi::k_adj_warp<4, 1>;
             StripTuner::Key key;
             StripTuner::Slot ts = tuned_height(P.tz, K0, d, bg, resident_warps(K0, 32, S), st, key);
-            fwi::AdjArgs args = adj_args(P, work, n, bg, snap + (size_t)(n - n0) * slot, res);
+            fwi::AdjArgs args = adj_args(P, work, n, bg, pn);
             args.tz = ts.tz;
             const dim3 grid = warp_grid(P, ts.tz, bg, 1);
             constexpr int B128 = fwi::minb(128, 32), B170 = fwi::minb(170, 32);
@@ -755,7 +746,10 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
                 }
             }
             g_tuner.finish(key, ts, st);
-            if (n % P.acc == 0) flush_acc(P, work, bg, st);
+            if (n % P.acc == 0) {
+                const int rc = flush_acc(P, work, bg, st);
+                if (rc) return rc;
+            }
         }
     }
     return FWI_OK;

@@ -194,47 +194,6 @@ __global__ void k_receiver_chain(const long long *__restrict__ idx, int n4, int 
     rl[k] = nx | (first ? CHAIN_FIRST : 0);
 }
 
-// Unique receiver cells (the first footprint entry of each cell's chain) listed by padded row,
-// for the adjoint launches that inject the residual while they write each row:
-// rrow[j] .. rrow[j+1] index the cells of row j in rcell, each (column, first entry).  One
-// block; rcur (Nz ints) is its scratch.  The order of the cells within a row is free: each
-// cell is a different address, injected by the one lane that owns it.
-constexpr int ROWS_THREADS = 1024;
-
-__global__ void __launch_bounds__(ROWS_THREADS) k_receiver_rows(const long long *__restrict__ idx,
-                                                                const int *__restrict__ rl, int n4, int Px, int Nz,
-                                                                int *__restrict__ rrow, int *__restrict__ rcur,
-                                                                int2 *__restrict__ rcell)
-{
-    __shared__ int part[ROWS_THREADS];
-    const int t = threadIdx.x;
-    for (int j = t; j < Nz; j += ROWS_THREADS) rcur[j] = 0;
-    __syncthreads();
-    for (int k = t; k < n4; k += ROWS_THREADS)
-        if (rl[k] & CHAIN_FIRST) atomicAdd(&rcur[(int)(idx[k] / Px)], 1);
-    __syncthreads();
-    // exclusive scan of the row counts: thread t takes rows [t*per, (t+1)*per)
-    const int per = (Nz + ROWS_THREADS - 1) / ROWS_THREADS, lo = min(t * per, Nz), hi = min(lo + per, Nz);
-    int own = 0;
-    for (int j = lo; j < hi; ++j) own += rcur[j];
-    part[t] = own;
-    __syncthreads();
-    if (t == 0) {
-        int run = 0;
-        for (int k = 0; k < ROWS_THREADS; ++k) { const int c = part[k]; part[k] = run; run += c; }
-        rrow[Nz] = run;
-    }
-    __syncthreads();
-    int run = part[t];
-    for (int j = lo; j < hi; ++j) { const int c = rcur[j]; rrow[j] = run; rcur[j] = run; run += c; }
-    __syncthreads();
-    for (int k = t; k < n4; k += ROWS_THREADS)
-        if (rl[k] & CHAIN_FIRST) {
-            const int j = (int)(idx[k] / Px), i = (int)(idx[k] - (long long)j * Px);
-            rcell[atomicAdd(&rcur[j], 1)] = make_int2(i, k);
-        }
-}
-
 // ------------------------------------------------------------ shared kernel arguments
 
 struct Model {
@@ -340,32 +299,78 @@ __global__ void __launch_bounds__(RED_THREADS) k_sum_final(const double *__restr
     if (threadIdx.x == 0) out[0] = acc;
 }
 
+// Knuth's TwoSum: s + v rounded, with the exact rounding error added to c (no FMA contraction:
+// every operation is an explicitly rounded add).  A run of these keeps the sum of FP32 values
+// as the unevaluated pair s + c, exact to about twice FP32 precision.
+__device__ __forceinline__ void two_sum(float &s, float &c, float v)
+{
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
 // Gradient accumulation in time: every adjoint launch adds one step's zero-lag products to
 // FP32 per-shot-slot fields (one red per address per launch, so the order is fixed); after a
-// chunk of steps the slots are flushed into FP64 running sums over shots and cleared.  Thread
-// t takes the float4 of cells 4t .. 4t+3 of every slot (Np is a multiple of 32): the slots are
-// summed in FP64 in slot order and the sum is added to the running sum.
-__global__ void k_acc_flush(float *__restrict__ accK, float *__restrict__ accBx, float *__restrict__ accBz,
-                            int nslots, long long Np, double *__restrict__ sK, double *__restrict__ sX,
-                            double *__restrict__ sZ)
+// chunk of steps the slots are flushed into FP64 running sums over shots (and then cleared by
+// the host with a memset).  A block of FLUSH_X x FLUSH_Y threads takes FLUSH_X float4 of cells
+// of field blockIdx.y (Np is a multiple of 32): thread (x, y) sums slots y, y + FLUSH_Y, ... with
+// TwoSum, the FLUSH_Y partial pairs are combined in y order -- a fixed order for a given slot
+// count -- and the pair is added to the FP64 running sum.  (The FP64 units of this GPU are few:
+// widening every slot value would make the flush FP64-bound; the compensated FP32 sum needs
+// four FP64 operations a cell.)
+constexpr int FLUSH_X = 32, FLUSH_Y = 8, FLUSH_UNROLL = 4;
+
+__global__ void __launch_bounds__(FLUSH_X * FLUSH_Y) k_acc_flush(const float *__restrict__ accK,
+                                                                 const float *__restrict__ accBx,
+                                                                 const float *__restrict__ accBz, int nslots, long long Np,
+                                                                 double *__restrict__ sK, double *__restrict__ sX,
+                                                                 double *__restrict__ sZ)
 {
-    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (e >= Np) return;
-    float *acc[3] = {accK, accBx, accBz};
-    double *sum[3] = {sK, sX, sZ};
+    __shared__ float ps[FLUSH_Y][FLUSH_X][4], pc[FLUSH_Y][FLUSH_X][4];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long e = ((long long)blockIdx.x * FLUSH_X + tx) * 4;
+    const float *__restrict__ acc = blockIdx.y == 0 ? accK : blockIdx.y == 1 ? accBx : accBz;
+    double *__restrict__ sum = blockIdx.y == 0 ? sK : blockIdx.y == 1 ? sX : sZ;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    if (e < Np)
+        for (int s0 = ty; s0 < nslots; s0 += FLUSH_Y * FLUSH_UNROLL) {
+            float4 v[FLUSH_UNROLL];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        for (int s = 0; s < nslots; ++s) {
-            float4 *q = reinterpret_cast<float4 *>(acc[f] + s * Np + e);
-            const float4 v = *q;
-            a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
-            *q = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < FLUSH_UNROLL; ++u) {   // independent loads first
+                const int sl = s0 + u * FLUSH_Y;
+                v[u] = sl < nslots ? __ldcs(reinterpret_cast<const float4 *>(acc + sl * Np + e))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < FLUSH_UNROLL; ++u)
+                if (s0 + u * FLUSH_Y < nslots) {
+                    two_sum(s[0], c[0], v[u].x);
+                    two_sum(s[1], c[1], v[u].y);
+                    two_sum(s[2], c[2], v[u].z);
+                    two_sum(s[3], c[3], v[u].w);
+                }
         }
-        double2 *o = reinterpret_cast<double2 *>(sum[f] + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ps[ty][tx][k] = s[k];
+        pc[ty][tx][k] = c[k];
+    }
+    __syncthreads();
+    if (ty == 0 && e < Np) {
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int y = 0; y < FLUSH_Y; ++y)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                two_sum(S[k], C[k], ps[y][tx][k]);
+                C[k] = __fadd_rn(C[k], pc[y][tx][k]);
+            }
+        double2 *o = reinterpret_cast<double2 *>(sum + e);
         const double2 lo = o[0], hi = o[1];
-        o[0] = make_double2(lo.x + a0, lo.y + a1);
-        o[1] = make_double2(hi.x + a2, hi.y + a3);
+        o[0] = make_double2(lo.x + ((double)S[0] + (double)C[0]), lo.y + ((double)S[1] + (double)C[1]));
+        o[1] = make_double2(hi.x + ((double)S[2] + (double)C[2]), hi.y + ((double)S[3] + (double)C[3]));
     }
 }
 

@@ -435,26 +435,17 @@ __global__ void __launch_bounds__(32 * FWD_WPB) k_fwd_batch(const __grid_constan
 //   accBz/accBx += u dt D+ p^n    (g_b = -accB)
 //   accK += p^n (pbar^n - d_p pbar^{n+1}) = p^n dt D- (b u)      (g_K = accK / K)
 // The last line pairs each pressure adjoint with its own snapshot one launch earlier than the
-// textbook form sum pbar^{n+1} (p^{n+1} - d_p p^n).  The trace-sampling transpose of the next
-// step, pbar^n += R^T r_{n-1}, and its receiver-cell remainder accK += (R^T r_{n-1}) p^n are
-// folded into the same launch: the lane that writes a receiver cell of pbar^n adds both (the
-// rows' receiver cells come from k_receiver_rows).  Only the first step's injection,
-// r_{nt-1} into the zero pbar^{nt}, is a launch of its own (k_adj_inject_k).
+// textbook form sum pbar^{n+1} (p^{n+1} - d_p p^n); the receiver-cell remainder
+// (R^T r_n) p^{n+1} is added by k_adj_inject_k.
 struct AdjArgs {
     const float *ap0, *avx0, *avz0;   // pbar^{n+1} (after injection), vbar^{n+1/2}
     float *ap1, *avx1, *avz1;         // pbar^n, new vbar
     Model mo;
     const float *pn;                  // p^n snapshots of the launch's shots
     float *accK, *accBx, *accBz;      // FP32 gradient accumulators of the launch's shots
-    const float *res;                 // [shots][nr][nt] residual of the launch's shots
-    const int *rrow;                  // [Nz + 1] first unique receiver cell of each padded row
-    const int2 *rcell;                // unique receiver cells by row: (column, first footprint entry)
-    const float *rw;                  // [nr][4] receiver weights
-    const int *rl;                    // footprint chains (k_receiver_chain)
     Dims d;
     Stencil st;
     int tz, nshots;
-    int nr, nt, inj;                  // inj: residual column injected into pbar^n (n - 1); < 0 none
 };
 
 // Shared memory of one adjoint warp.
@@ -465,33 +456,7 @@ struct AdjSmem {
     float stg[ADJ_WPD + 1][7][WROW];      // pbar, K (row f); vbar_z, bz (row r); vbar_x, bx, pbar (row j)
     float bur[2][WROW];               // bx u_x rows
     float scl[ADJ_WPD + 1][4];            // az(f), azh(r), az(j) of each stage
-    int rsc[ADJ_WPD + 1][2];              // receiver cells of row j: rrow[j], rrow[j + 1]
 };
-
-// Adds the receiver injection of residual column a.inj to the new pbar^n float4 `an` of row
-// cells c0 .. c0+3 and its K-gradient term (R^T r) p^n to `gk`, for the unique receiver
-// cells e0 .. e1 of the row.  Each cell sums its footprint chain in receiver order, the
-// same sum for every strip and launch shape.
-__device__ __forceinline__ void inject_row(const AdjArgs &a, int s, int e0, int e1, int c0, const float4 &p,
-                                           float4 &an, float4 &gk)
-{
-    const int n4 = 4 * a.nr;
-    const float *rs = a.res + (long long)s * a.nr * a.nt + a.inj;
-    for (int e = e0; e < e1; ++e) {
-        const int2 c = __ldg(a.rcell + e);
-        const int q = c.x - c0;
-        if (q < 0 || q > 3) continue;
-        int k = c.y;
-        float v = __ldg(a.rw + k) * __ldg(rs + (long long)(k >> 2) * a.nt);
-        for (k = __ldg(a.rl + k) & (CHAIN_FIRST - 1); k < n4; k = __ldg(a.rl + k) & (CHAIN_FIRST - 1))
-            v += __ldg(a.rw + k) * __ldg(rs + (long long)(k >> 2) * a.nt);
-        addc(an, q, v);
-        if (q == 0) gk.x = fmaf(v, p.x, gk.x);
-        else if (q == 1) gk.y = fmaf(v, p.y, gk.y);
-        else if (q == 2) gk.z = fmaf(v, p.z, gk.z);
-        else gk.w = fmaf(v, p.w, gk.w);
-    }
-}
 
 template <int M>
 __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjSmem<M> &sh)
@@ -516,7 +481,6 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
     const float4 axv = ldg_if(mo.ax + L.mc, L.in), axhv = ldg_if(mo.axh + L.mc, L.in);
     const float4 axe = ldg_if(mo.ax + L.ec, L.ein);
     const int z0 = sp.z0, zend = min(z0 + tz, d.Nz), f0 = z0 - R;
-    const bool inj = a.inj >= 0;
     // rows the strip's outputs depend on (the others stream in as zeros, reading nothing):
     // pbar / K rows f >= z0 - 2M + 1, forward p rows f >= z0 - M + 1, u_z rows r >= z0 - M,
     // u_x rows j >= z0
@@ -531,9 +495,6 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
             cp4(&sh.scl[ss][0], mo.az, f, vf);
             cp4(&sh.scl[ss][1], mo.azh, r, vr);
             cp4(&sh.scl[ss][2], mo.az, j, vj);
-            const float *rr = reinterpret_cast<const float *>(a.rrow);
-            cp4(&sh.rsc[ss][0], rr, j, vj && inj);
-            cp4(&sh.rsc[ss][1], rr, j + 1, vj && inj);
         }
         cp16(prow + L.mo, PN, of + L.mc, vp && L.in);
         cp16(sg[0] + L.mo, A0, of + L.mc, vf && L.in);
@@ -617,13 +578,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
             for (int k = 1; k <= M; ++k)   // bq[q] is row j - M + q
                 dv = ptap(st.c[k - 1], bq[M + k - 1], bq[M - k], dv);
             const float4 dp = pmul(az, axv);
-            float4 an = pfma(dp, ld4(sg[6] + L.mo), dv);
+            st4(A1 + j * d.Px + L.mc, pfma(dp, ld4(sg[6] + L.mo), dv));
             // pbar^n - d_p pbar^{n+1} is exactly the divergence term dv
-            float4 gk = pmul(pq[0], dv);
-            const int e0 = sh.rsc[S(0)][0], e1 = sh.rsc[S(0)][1];
-            if (e0 < e1) inject_row(a, sp.s, e0, e1, L.mc, pq[0], an, gk);
-            st4(A1 + j * d.Px + L.mc, an);
-            red_add4(GK + j * d.Px + L.mc, gk);
+            red_add4(GK + j * d.Px + L.mc, pmul(pq[0], dv));
         }
         P.next();
         S.next();
