@@ -103,6 +103,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-engine", action="store_true",
+                    help="skip the batching and serving measurements that follow the main one")
+    ap.add_argument("--engine-jobs", type=int, default=32,
+                    help="batching measurement: the first N of the 256 uneven jobs")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="serving measurement: requests of the light Poisson stream")
     ap.add_argument("--profile-every", type=int, default=8,
                     help="time one launch in N of each kernel with CUDA events inside the timed region")
     ap.add_argument("--tile", type=int, default=0,
@@ -413,6 +419,16 @@ def main():
         out["plain_per_shot"] = plain_per_shot(fwi, I, g, w0, dev, nt)
     if not args.no_e2e:
         out["e2e"] = end_to_end(fwi, I, g, w0, dev, nt, ns, args, rank, world, (ws_model, ws_grad, ws_born))
+    if rank == 0 and world == 1 and not args.no_engine:
+        # the batching engine and the serving loop (the workloads' own sizes; each with its own
+        # clock record): the main workspaces go first
+        del ws_model, ws_grad, ws_born
+        torch.cuda.empty_cache()
+        from paper_1804_01184_gb300 import workloads
+        out["batching"] = workloads.run_batch(args.engine_jobs, Clocks)
+        torch.cuda.empty_cache()
+        out["serving"] = workloads.run_serve(args.serve_requests, 200.0, "light", Clocks)[0]
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu:
         os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
         v, dt, _ = cpu_sample(300)

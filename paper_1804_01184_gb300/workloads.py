@@ -66,10 +66,13 @@ def _drain(eng, ticket_jobs):
     return time.perf_counter() - t0, launches, out
 
 
-def bench_batch(args, Clocks):
+def run_batch(njobs, Clocks, profile=False, total=256):
+    """The first `njobs` of inputs.batch_jobs(total, seed=0) through the engine: their forward
+    models (observed data), then their misfit gradients at the background, each phase one engine
+    run; against the plain per-shot GPU path on a sample of the same jobs.  Returns a dict."""
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    jobs = I.batch_jobs(args.jobs, seed=0)
+    jobs = I.batch_jobs(total, seed=0)[:njobs]
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     staged = [dict(a=d(w.xi_a), b=d(w.xi_b), src=d(w.src_xy), rec=d(w.rec_xy), wav=d(w.wavelet),
                    zero=torch.zeros((w.nz, w.nx), dtype=torch.float32, device=dev)) for w in jobs]
@@ -83,7 +86,7 @@ def bench_batch(args, Clocks):
 
     clocks = Clocks(0)
     clocks.start()
-    if args.profile:
+    if profile:
         kernel_profile(True, every=8)
     # phase A: observed data of the true models (all shots of a job in one group when it fits)
     tickets = [eng.submit_model(grid_of(w), w.pz, s["a"], s["b"], s["src"], s["wav"], s["rec"],
@@ -95,30 +98,45 @@ def bench_batch(args, Clocks):
                                    work_budget=grad_budget) for w, s, dd in zip(jobs, staged, data)]
     t_grad, l_grad, res = _drain(eng, tickets)
     clk = clocks.stop()
-    prof = kernel_profile(False) if args.profile else None
+    prof = kernel_profile(False) if profile else None
     finite = all(bool(torch.isfinite(res[t].grads).all()) for t in tickets[:8])
     eng.close()
+    del eng, res
+    torch.cuda.empty_cache()
 
     value = (total_fwd + 2 * total_fwd) / (t_model + t_grad) / 1e9
     plain = plain_per_shot_batch(jobs, staged, data, dev)
     out = {
-        "metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": 1, "steps": 1,
-        "warmup": 0, "ms_per_step": round(1e3 * (t_model + t_grad), 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch-{args.jobs}-uneven", "jobs": args.jobs,
-                   "sizes": "square 128^2..1024^2 (+40-cell sponge), 500-4000 steps, 1-32 shots, 8th order",
-                   "arena_gb": round(arena / 2**30, 1), "gradient_budget_gb": round(grad_budget / 2**30, 2),
-                   "l2": "working set larger than L2"},
+        "value": round(value, 3), "unit": "Gcell-updates/s", "seconds": round(t_model + t_grad, 2),
+        "jobs": njobs, "sample": f"the first {njobs} of batch_jobs({total}, seed 0)" if njobs < total else None,
+        "sizes": "square 128^2..1024^2 (+40-cell sponge), 500-4000 steps, 1-32 shots, 8th order",
+        "arena_gb": round(arena / 2**30, 1), "gradient_budget_gb": round(grad_budget / 2**30, 2),
         "forward": {"value": round(total_fwd / t_model / 1e9, 3), "seconds": round(t_model, 2),
                     "launches": l_model},
         "gradient": {"value": round(2 * total_fwd / t_grad / 1e9, 3), "seconds": round(t_grad, 2),
-                     "gradients_per_s": round(args.jobs / t_grad, 3), "launches": l_grad, "finite": finite},
+                     "gradients_per_s": round(njobs / t_grad, 3), "launches": l_grad, "finite": finite},
         "plain_per_shot": plain,
         "speedup_vs_plain": round(value / plain["value"], 2) if plain["value"] else None,
         "gpu_launches": l_model + l_grad, "clocks": clk,
     }
     if prof:
         out["profile"] = prof
+    return out
+
+
+def bench_batch(args, Clocks):
+    r = run_batch(args.jobs, Clocks, profile=args.profile)
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": "Gcell-updates/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": round(1e3 * r["seconds"], 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch-{args.jobs}-uneven", "jobs": args.jobs, "sizes": r["sizes"],
+                   "arena_gb": r["arena_gb"], "gradient_budget_gb": r["gradient_budget_gb"],
+                   "l2": "working set larger than L2"},
+        **{k: r[k] for k in ("forward", "gradient", "plain_per_shot", "speedup_vs_plain", "gpu_launches", "clocks")},
+    }
+    if "profile" in r:
+        out["profile"] = r["profile"]
     print(json.dumps(out), flush=True)
 
 
@@ -197,37 +215,56 @@ def serve_plain(requests, arrivals):
             "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2)}
 
 
-def bench_serve(args, Clocks):
+def run_serve(requests, rate, sizes, Clocks, profile=False):
+    """A seeded Poisson stream of `requests` mixed forward / Born / gradient requests at `rate`
+    per second through the continuous-batching loop (sizes 'light' or 'batch'); the light stream
+    is also served one request at a time through the single-job calls.  Returns a dict."""
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    kw = LIGHT if args.sizes == "light" else {}
-    reqs = serve_requests(args.requests, seed=1, **kw)
-    arrivals = I.poisson_arrivals(len(reqs), args.rate, seed=2)
+    kw = LIGHT if sizes == "light" else {}
+    reqs = serve_requests(requests, seed=1, **kw)
+    arrivals = I.poisson_arrivals(len(reqs), rate, seed=2)
     free, _ = torch.cuda.mem_get_info(dev)
     arena = int(free * 0.6) // 256 * 256
     # the engine: warm-up on the first few requests, then the timed stream
     S.serve(reqs[:4], np.zeros(4), arena)
     clocks = Clocks(0)
     clocks.start()
-    if args.profile:
+    if profile:
         kernel_profile(True, every=8)
     stats, _ = S.serve(reqs, arrivals, arena)
-    prof = kernel_profile(False) if args.profile else None
+    prof = kernel_profile(False) if profile else None
     clk = clocks.stop()
-    plain = serve_plain(reqs, arrivals) if args.sizes == "light" else None
+    plain = serve_plain(reqs, arrivals) if sizes == "light" else None
     upd = sum(PASSES[r.kind] * cells(r.workload) for r in reqs)
+    out = {"requests": len(reqs), "rate_per_s": rate, "mix": "forward / Born / gradient, uniform",
+           "sizes": ("square 128^2..256^2, 500-1000 steps, 1-4 shots" if sizes == "light" else
+                     "square 128^2..1024^2, 500-4000 steps, 1-32 shots"),
+           "arena_gb": round(arena / 2**30, 1),
+           "gcell_per_s": round(upd / stats["wall_s"] / 1e9, 3),
+           **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()},
+           "plain_one_at_a_time": plain, "clocks": clk}
+    if plain:
+        out["speedup_vs_plain"] = round(stats["req_per_s"] / plain["req_per_s"], 2)
+    if prof:
+        out["profile"] = prof
+    return out, reqs, arena
+
+
+def bench_serve(args, Clocks):
+    r, reqs, arena = run_serve(args.requests, args.rate, args.sizes, Clocks, profile=args.profile)
+    stats = {k: r[k] for k in ("requests", "wall_s", "req_per_s", "p50_ms", "p99_ms", "mean_queue_ms", "launches",
+                                "max_running")}
+    kw = LIGHT if args.sizes == "light" else {}
     out = {
-        "metric": METRIC, "value": round(upd / stats["wall_s"] / 1e9, 3), "unit": "Gcell-updates/s",
+        "metric": METRIC, "value": r["gcell_per_s"], "unit": "Gcell-updates/s",
         "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * stats["wall_s"], 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serve-{args.sizes}-poisson{args.rate:g}", "requests": len(reqs),
-                   "rate_per_s": args.rate, "mix": "forward / Born / gradient, uniform",
-                   "sizes": ("square 128^2..256^2, 500-1000 steps, 1-4 shots" if args.sizes == "light" else
-                             "square 128^2..1024^2, 500-4000 steps, 1-32 shots"),
-                   "arena_gb": round(arena / 2**30, 1)},
-        "serving": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()},
-        "plain_one_at_a_time": plain,
-        "gpu_launches": stats["launches"], "clocks": clk,
+                   "rate_per_s": args.rate, "mix": r["mix"], "sizes": r["sizes"], "arena_gb": r["arena_gb"]},
+        "serving": stats,
+        "plain_one_at_a_time": r["plain_one_at_a_time"],
+        "gpu_launches": stats["launches"], "clocks": r["clocks"],
     }
     if args.capacity_run > 0:
         # a second stream at 80 % of the throughput the first one reached
@@ -237,8 +274,8 @@ def bench_serve(args, Clocks):
         st2, _ = S.serve(reqs2, arr2, arena)
         out["at_80pct_capacity"] = {"rate_per_s": round(rate, 3),
                                     **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in st2.items()}}
-    if prof:
-        out["profile"] = prof
+    if "profile" in r:
+        out["profile"] = r["profile"]
     print(json.dumps(out), flush=True)
 
 
