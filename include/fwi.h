@@ -201,6 +201,18 @@ int fwi_status_noalloc(void *stream);
  * Gradients are identical either way. */
 int fwi_set_checkpoint(int every);
 
+/* Phase ranges for timeline tools (no counterpart in the paper).  enable = 1: every operation
+ * marks the host thread's enqueueing of its phases with NVTX ranges ("fwi:model_build",
+ * "fwi:forward", "fwi:recompute", "fwi:adjoint", "fwi:reduce", "fwi:born",
+ * "fwi:engine_iteration"), visible to timeline profilers; 0 (default): none.  Results are
+ * identical either way. */
+int fwi_trace(int enable);
+
+/* Ranges opened per phase since the last report, one "name count" line each, written to buf
+ * (at most len - 1 bytes, NUL-terminated; buf may be NULL to only reset); returns the length of
+ * the full report. */
+int fwi_trace_report(char *buf, size_t len);
+
 /* Length of the FP32 accumulation chunks of the gradient (no counterpart in the paper; the
  * time integral of the zero-lag cross-correlation of Sec. "Modelling and Inversion" is a sum
  * over all steps).  steps > 0: plans made afterwards flush the FP32 per-shot accumulators
@@ -280,6 +292,16 @@ int fwi_engine_submit(fwi_engine *engine, const fwi_job *job, long long *ticket)
  * submitted between calls).  Returns FWI_OK or the first failure (FWI_ECUDA, ...) of the work
  * it enqueued; after a failure the engine's jobs are undefined: destroy it. */
 int fwi_engine_run(fwi_engine *engine, int iterations, long long *done, int max_done, int *ndone);
+
+/* Cancels a job that is queued or running (a request the caller no longer wants; no
+ * counterpart in the paper).  A queued job leaves the queue.  A running job stops being
+ * advanced and its arena block returns to the free list at once: the work already enqueued
+ * for it on the engine's stream still runs, before anything enqueued later, so the block is
+ * reused safely; its outputs are left incomplete and its ticket never comes back as done.
+ * The job's input and output arrays stay in use until the engine's stream has passed this
+ * call (synchronise it, or record an event, before freeing them).  The other jobs' results
+ * do not change.  Returns FWI_EINVAL for a ticket that is not queued or running. */
+int fwi_engine_cancel(fwi_engine *engine, long long ticket);
 
 /* Jobs queued, running (admitted, not retired) and retired but not yet reported as done;
  * bytes of the arena in use. */

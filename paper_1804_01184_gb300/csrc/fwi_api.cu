@@ -2,8 +2,10 @@
 // The C ABI is declared in include/fwi.h.  Every arithmetic step of the method runs in the
 // kernels of fwi_kernels.cuh; this file only plans memory and orders launches.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cmath>
 #include <cstdint>
@@ -84,6 +86,28 @@ struct Profiler {
     }
 };
 Profiler g_prof;
+
+// Phase ranges for timeline tools (NVTX), on while fwi_trace(1): each marks the host thread's
+// enqueueing of one phase of an operation; fwi_trace_report() counts the ranges opened.
+enum Phase { PH_MODEL_BUILD, PH_FORWARD, PH_RECOMPUTE, PH_ADJOINT, PH_REDUCE, PH_BORN, PH_ENGINE, PH_COUNT };
+const char *const kPhaseName[PH_COUNT] = {"fwi:model_build", "fwi:forward", "fwi:recompute", "fwi:adjoint",
+                                          "fwi:reduce", "fwi:born", "fwi:engine_iteration"};
+std::atomic<bool> g_trace{false};
+std::atomic<long long> g_trace_count[PH_COUNT];
+
+struct TraceRange {
+    bool on;
+    explicit TraceRange(Phase p) : on(g_trace.load(std::memory_order_relaxed))
+    {
+        if (!on) return;
+        nvtxRangePushA(kPhaseName[p]);
+        g_trace_count[p].fetch_add(1, std::memory_order_relaxed);
+    }
+    ~TraceRange()
+    {
+        if (on) nvtxRangePop();
+    }
+};
 
 // Launch-shape overrides set by fwi_set_tile (0: built-in defaults); read when a plan is made.
 int g_tile_tz = 0;
@@ -285,6 +309,7 @@ int cuda_fail(cudaError_t e, const char *what)
 int setup(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float *xb,
           const fwi_sources *src, const fwi_receivers *rec, void *work, cudaStream_t st)
 {
+    TraceRange tr(PH_MODEL_BUILD);
     const fwi::Dims &d = P.d;
     const double sum_c = P.M == 2 ? 9.0 / 8.0 + 1.0 / 24.0
                                   : 1225.0 / 1024.0 + 245.0 / 3072.0 + 49.0 / 5120.0 + 5.0 / 7168.0;
@@ -644,6 +669,7 @@ int plan_for(Plan &P, const fwi_grid *g, fwi_op op, int ns, int nr, size_t work_
 int forward_group(const Plan &P, void *work, cudaStream_t st, const float *wav, int s0, int bg,
                   float *traces, bool with_hist)
 {
+    TraceRange tr(PH_FORWARD);
     const Fwd f{P, work, st, wav};
     const size_t bf = (size_t)bg * P.d.Np * sizeof(float);
     const size_t slot = (size_t)P.B * P.d.Np;   // floats between snapshot slots
@@ -711,6 +737,7 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
     for (int k = P.nseg - 1; k >= 0; --k) {
         const int n0 = k * P.C, n1 = std::min(n0 + P.C, P.nt);
         if (k < P.nseg - 1) {   // recompute the segment from its checkpoint
+            TraceRange tr(PH_RECOMPUTE);
             const float *ck = at<float>(work, P.ckpt) + (size_t)k * 3 * slot;
             CK(cudaMemcpyAsync(snap, ck, bf, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(at<float>(work, P.vx[n0 & 1]), ck + slot, bf, cudaMemcpyDeviceToDevice, st));
@@ -718,6 +745,7 @@ int adjoint_group(const Plan &P, void *work, cudaStream_t st, const float *wav, 
             for (int n = n0; n < n1; ++n)
                 f.step(n, s0, bg, snap + (size_t)(n - n0) * slot, snap + (size_t)(n + 1 - n0) * slot);
         }
+        TraceRange tr(PH_ADJOINT);
         for (int n = n1 - 1; n >= n0; --n) {
             const float *pn = snap + (size_t)(n - n0) * slot, *pn1 = snap + (size_t)(n + 1 - n0) * slot;
             if (P.nr > 0)   // pbar^{n+1} += R^T r_n, with its K-gradient term (R^T r_n) p^{n+1}
@@ -767,6 +795,7 @@ int clear_acc(const Plan &P, void *work, cudaStream_t st)
 int finalize_grad(const Plan &P, const fwi_grid *g, int pz, const float *xa, const float *xb, void *work,
                   double *grads, cudaStream_t st)
 {
+    TraceRange tr(PH_REDUCE);
     const fwi::Dims &d = P.d;
     dim3 b2(32, 8), gp((d.Nx + 31) / 32, (d.Nz + 7) / 8), gq((d.nx + 31) / 32, (d.nz + 7) / 8);
     LAUNCH(fwi::k_grad_cells, gp, b2, 0, st, at<float>(work, P.K), at<float>(work, P.bx), at<float>(work, P.bz), d,
@@ -883,6 +912,7 @@ int fwi_born(const fwi_grid *g, fwi_param pz, const float *xi_a, const float *xi
     const fwi::Model mo = model_of(P, work);
     const fwi::Pert pe{at<float>(work, P.dK), at<float>(work, P.dbx), at<float>(work, P.dbz)};
     for (int gi = 0; gi < P.ngroups; ++gi) {
+        TraceRange tr(PH_BORN);
         const int s0 = gi * P.B, bg = std::min(P.B, P.ns - s0);
         const size_t bf = (size_t)bg * d.Np * sizeof(float);
         for (size_t off : {P.p[0], P.vx[0], P.vz[0], P.dp[0], P.dvx[0], P.dvz[0]})
@@ -1000,6 +1030,28 @@ int fwi_set_checkpoint(int every)
     if (every < 0) return fail(FWI_EINVAL, "checkpoint interval must be >= 0");
     g_ckpt_every = every;
     return FWI_OK;
+}
+
+int fwi_trace(int enable)
+{
+    if (enable < 0) return fail(FWI_EINVAL, "trace switch must be 0 or 1");
+    g_trace.store(enable != 0);
+    return FWI_OK;
+}
+
+int fwi_trace_report(char *buf, size_t len)
+{
+    std::string out;
+    char line[96];
+    for (int p = 0; p < PH_COUNT; ++p) {
+        snprintf(line, sizeof line, "%s %lld\n", kPhaseName[p], g_trace_count[p].exchange(0));
+        out += line;
+    }
+    if (buf && len) {
+        strncpy(buf, out.c_str(), len - 1);
+        buf[len - 1] = 0;
+    }
+    return (int)out.size();
 }
 
 int fwi_set_accumulation(int steps)

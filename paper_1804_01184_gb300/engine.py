@@ -44,6 +44,7 @@ def _lib():
         L.fwi_engine_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_size_t)]
         L.fwi_engine_destroy.argtypes = [vp]
+        L.fwi_engine_cancel.argtypes = [vp, C.c_longlong]
         _bound = True
     return L
 
@@ -68,6 +69,7 @@ class Engine:
         F._raise(_lib().fwi_engine_create(C.byref(self._h), C.c_void_p(self.arena.data_ptr()),
                                           self.arena.numel(), C.c_void_p(self.stream.cuda_stream)))
         self._jobs: dict[int, tuple] = {}
+        self._cancelled: list[tuple] = []   # (event, tensors) of cancelled jobs still on the stream
 
     # ---------------------------------------------------------------- submission
     def _submit(self, kind, grid, pz, xi_a, xi_b, src_xy, wavelet, rec_xy, dxi=None, out=None, data=None,
@@ -117,10 +119,20 @@ class Engine:
         return self._submit(JOB_GRADIENT, grid, pz, xi_a, xi_b, src_xy, wavelet, rec_xy, data=data,
                             work_budget=work_budget)
 
+    def cancel(self, ticket: int):
+        """Cancels a queued or running job (fwi_engine_cancel): it never comes back from run();
+        its tensors are kept until the engine's stream has passed the cancellation."""
+        F._raise(_lib().fwi_engine_cancel(self._h, int(ticket)))
+        res, held = self._jobs.pop(int(ticket))
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        self._cancelled.append((ev, (res, held)))
+
     # ------------------------------------------------------------------- running
     def run(self, iterations: int = 64, max_done: int = 4096) -> list[Result]:
         """Advances the engine; returns the jobs that finished (results complete on the device,
         ordered before later work on the engine's stream)."""
+        self._cancelled = [c for c in self._cancelled if not c[0].query()]
         done = (C.c_longlong * max_done)()
         nd = C.c_int()
         F._raise(_lib().fwi_engine_run(self._h, int(iterations), done, int(max_done), C.byref(nd)))

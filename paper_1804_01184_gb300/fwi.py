@@ -5,7 +5,7 @@ PyTorch supplies device memory (inputs, outputs and the scratch workspace) and s
 The functions carry the C names: ``fwi_model``, ``fwi_born``, ``fwi_adjoint``,
 ``fwi_gradient`` (optionally weighted per trace), ``fwi_misfit``, ``fwi_workspace_bytes``,
 ``fwi_status``, ``fwi_model_noalloc``, ``fwi_status_noalloc``, ``fwi_set_tile``, ``fwi_set_checkpoint``,
-``fwi_set_accumulation``.
+``fwi_set_accumulation``, ``fwi_trace``.
 
 There is no fallback: if libfwi.so has not been built (``paper_1804_01184_gb300.build``)
 or no CUDA device is present, these functions raise.
@@ -85,6 +85,8 @@ def lib():
             L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
             L.fwi_set_checkpoint.argtypes = [C.c_int]
             L.fwi_set_accumulation.argtypes = [C.c_int]
+            L.fwi_trace.argtypes = [C.c_int]
+            L.fwi_trace_report.argtypes = [C.c_char_p, C.c_size_t]
             L.fwi_model_noalloc.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp]
             L.fwi_status_noalloc.argtypes = [vp]
             L.fwi_profile.argtypes = [C.c_int]
@@ -175,6 +177,22 @@ def fwi_set_checkpoint(every: int = 0):
 def fwi_set_accumulation(steps: int = 0):
     """Adjoint steps per FP32 gradient-accumulation chunk for plans made afterwards (0 = 64)."""
     _raise(lib().fwi_set_accumulation(int(steps)))
+
+
+def fwi_trace(enable: bool = True):
+    """NVTX phase ranges on (True) or off for later operations on any thread."""
+    _raise(lib().fwi_trace(int(bool(enable))))
+
+
+def trace_report() -> dict:
+    """Ranges opened per phase since the last report ({phase: count}); resets the counts."""
+    buf = C.create_string_buffer(1 << 12)
+    lib().fwi_trace_report(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt = line.rsplit(" ", 1)
+        out[name] = int(cnt)
+    return out
 
 
 def launch_count() -> int:

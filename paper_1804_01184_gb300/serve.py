@@ -11,7 +11,9 @@ until the caller reads them.
 
 The loop records, per request, the arrival time, the submission time and the time its
 result was complete on the device (observed by the engine's completion event), and reports
-throughput and latency percentiles.
+throughput and latency percentiles.  A request may carry a deadline: when it has not
+finished that long after its arrival, the loop cancels it in the engine (queued or running),
+its workspace returns to the arena and its result is dropped; the others are unaffected.
 """
 from __future__ import annotations
 
@@ -32,6 +34,7 @@ class Request:
     dxi: tuple | None = None     # Born perturbation (host arrays)
     data: object = None          # gradient: observed traces (host array)
     work_budget: int | None = None   # None: the serving loop's default budget
+    deadline_s: float | None = None  # cancel when not done this long after arrival
 
 
 def _pinned(a):
@@ -83,6 +86,7 @@ def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=F
     t_done = np.full(n, np.nan)
     ticket_of = {}
     results = [None] * n
+    cancelled = np.zeros(n, bool)
     nxt = 0
     t0 = time.perf_counter()
     launches = 0
@@ -94,8 +98,15 @@ def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=F
             ticket_of[_submit(eng, r, staged[nxt], budget if r.work_budget is None else r.work_budget)] = nxt
             t_sub[nxt] = time.perf_counter() - t0
             nxt += 1
+        for t, k in list(ticket_of.items()):    # requests past their deadline
+            dl = requests[k].deadline_s
+            if dl is not None and now - arrivals[k] > dl:
+                eng.cancel(t)
+                del ticket_of[t]
+                cancelled[k] = True
         if not ticket_of:                       # idle until the next arrival
-            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+            if nxt < n:
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
             continue
         for res in eng.run(iterations_per_call):
             k = ticket_of.pop(res.ticket)
@@ -106,9 +117,12 @@ def serve(requests, arrivals, arena_bytes, iterations_per_call=8, keep_results=F
         max_running = max(max_running, eng.info()["running"])
     wall = time.perf_counter() - t0
     eng.close()
-    lat = t_done - arrivals[:n]
-    stats = dict(requests=n, wall_s=wall, req_per_s=n / wall,
-                 p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+    ok = ~cancelled
+    lat = (t_done - arrivals[:n])[ok]
+    nok = int(ok.sum())
+    stats = dict(requests=n, wall_s=wall, req_per_s=nok / wall,
+                 p50_ms=float(np.percentile(lat, 50) * 1e3) if nok else float("nan"),
+                 p99_ms=float(np.percentile(lat, 99) * 1e3) if nok else float("nan"),
                  mean_queue_ms=float(np.mean(t_sub - arrivals[:n]) * 1e3), launches=launches,
-                 max_running=max_running)
+                 max_running=max_running, cancelled=int(cancelled.sum()))
     return stats, results

@@ -223,3 +223,36 @@ def test_many_gradients_overflow_the_per_receiver_table(L):
     for t, (k, w, x, b) in zip(tickets, jobs):
         assert_same(outputs(res[t]), single(F, k, w, x, b))
     E.close()
+
+
+def test_cancel_running_and_queued_jobs(L):
+    """fwi_engine_cancel: a running job stops, its arena block is free at once and its ticket
+    never comes back; a queued job leaves the queue; every other job's result equals the single
+    call bitwise, also the job admitted into the cancelled job's memory."""
+    F, Eng = L
+    kind, case, _ = MIX[4]
+    jobs = [(kind, *make_inputs(kind, dict(case, seed=800 + s)), 0) for s in range(5)]
+    need = F.fwi_workspace_bytes(gpu_grid(jobs[0][1]), jobs[0][1].ns, jobs[0][1].nr, OPS[kind], 0)
+    E = Eng.Engine(2 * need + need // 2)           # room for two jobs at a time
+    E.arena.fill_(0xFF)
+    torch.cuda.synchronize()
+    tickets = [submit(E, k, w, x, b) for k, w, x, b in jobs]
+    E.run(3)                                        # jobs 0 and 1 are running, 2..4 queued
+    st = E.info()
+    assert st["running"] == 2 and st["queued"] == 3
+    used = st["arena_used"]
+    E.cancel(tickets[1])                            # running
+    assert E.info()["running"] == 1 and E.info()["arena_used"] < used
+    E.cancel(tickets[3])                            # queued (admission waits for the next run)
+    assert E.info()["queued"] == 2
+    with pytest.raises(F.FwiError):
+        E.cancel(tickets[1])                        # already cancelled
+    res = {r.ticket: r for r in E.drain(16)}
+    assert sorted(res) == [tickets[0], tickets[2], tickets[4]]
+    assert E.info()["arena_used"] == 0
+    for t in (0, 2, 4):
+        k, w, x, b = jobs[t]
+        assert_same(outputs(res[tickets[t]]), single(F, k, w, x, b))
+    with pytest.raises(F.FwiError):
+        E.cancel(tickets[0])                        # finished
+    E.close()

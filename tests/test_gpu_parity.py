@@ -457,3 +457,31 @@ def test_profile_sampling_counts_every_launch_and_times_one_in_n(F):
         assert float(ms) > 0
         total += seen
     assert total == launched
+
+
+def test_trace_ranges_per_phase(F):
+    """fwi_trace(1): one NVTX range per phase -- the model build, each group's forward, each
+    checkpoint segment's recompute and adjoint, the reduction; results unchanged."""
+    w = I.small_case(seed=27, nx=44, nz=40, nt=90, order=8, sponge=5, ns=3, nr=4)
+    g = gpu_grid(w)
+    data = I.random_like((w.ns, w.nr, w.nt), 28, 1e3)
+    try:
+        F.fwi_set_checkpoint(30)                      # 3 segments
+        work = F.workspace(g, 2, w.nr, F.OP_GRADIENT, 1 << 40)   # sized for 2 shots: several groups
+        G0 = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, data, work=work)[1].clone()
+        F.trace_report()
+        F.fwi_trace(True)
+        G1 = F.fwi_gradient(g, w.pz, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy, data, work=work)[1]
+        F.fwi_born(g, w.pz, w.xi_a, w.xi_b, w.xi_a, w.xi_b, w.src_xy, w.wavelet, w.rec_xy)
+        rep = F.trace_report()
+    finally:
+        F.fwi_trace(False)
+        F.fwi_set_checkpoint(0)
+    assert torch.equal(G0, G1)
+    groups = rep["fwi:forward"]                       # one forward range per shot group
+    assert groups >= 2
+    assert rep["fwi:model_build"] == 2                # the gradient and the Born call
+    assert rep["fwi:adjoint"] == groups * 3
+    assert rep["fwi:recompute"] == groups * 2
+    assert rep["fwi:reduce"] == 1
+    assert rep["fwi:born"] >= 1

@@ -77,3 +77,26 @@ def test_stream_results_equal_alone_and_oracle(L):
             for pz in range(5):
                 for c in range(2):
                     assert rel_l2(got[pz, c], G[pz, c]) <= GRAD_TOL
+
+
+def test_deadlines_cancel_requests_and_leave_the_rest_unchanged(L):
+    """Requests whose deadline passes are cancelled in the engine (queued or running); the
+    others finish with the results they get alone."""
+    F, Eng, S, W = L
+    from paper_1804_01184_gb300 import inputs as I
+    reqs = W.serve_requests(12, seed=19, **SIZES)
+    for r in reqs[1::3]:
+        r.deadline_s = 0.0                                 # cancelled on the loop's next pass
+    arrivals = I.poisson_arrivals(len(reqs), 400.0, seed=4)
+    stats, results = S.serve(reqs, arrivals, ARENA, keep_results=True)
+    gone = [k for k in range(len(reqs)) if results[k] is None]
+    assert stats["cancelled"] == len(gone) >= 1
+    assert set(gone) <= set(range(1, len(reqs), 3))
+    torch.cuda.synchronize()
+    for r, res in zip(reqs, results):
+        if res is None:
+            continue
+        ref = single(F, Eng, S, r)
+        got = (res.traces,) if res.traces is not None else (res.misfit, res.grads)
+        for x, y in zip(got, ref):
+            assert torch.equal(x, y)
