@@ -593,8 +593,9 @@ fwi::Tail tail_of(const Plan &P, void *work, const float *field, float *traces, 
 
 fwi::Model model_of(const Plan &P, void *work)
 {
-    return fwi::Model{at<float>(work, P.K), at<float>(work, P.bx), at<float>(work, P.bz), at<float>(work, P.ax),
-                      at<float>(work, P.axh), at<float>(work, P.az), at<float>(work, P.azh)};
+    return fwi::Model{at<float>(work, P.K),   at<float>(work, P.bx), at<float>(work, P.bz),
+                      at<float>(work, P.ax),  at<float>(work, P.axh), at<float>(work, P.az),
+                      at<float>(work, P.azh), at<int>(work, P.status)};
 }
 
 struct Fwd {
@@ -1001,6 +1002,8 @@ int fwi_status(void *work, void *stream)
     CK(cudaStreamSynchronize(st));
     if (h & fwi::ST_EINVAL) return fail(FWI_EINVAL, "a contrast has 1 + xi <= 0 or a position lies outside the physical grid");
     if (h & fwi::ST_ECFL) return fail(FWI_ECFL, "dt exceeds the stability limit of the stencil for this model");
+    if (h & fwi::ST_EBOUNDS)
+        return fail(FWI_EINVAL, "a bounds check of the checked build caught an out-of-range access (skipped)");
     return FWI_OK;
 }
 

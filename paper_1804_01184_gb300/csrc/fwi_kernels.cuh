@@ -33,7 +33,23 @@ struct Stencil {
 };
 
 // status bits recorded by the kernels
-enum : int { ST_EINVAL = 1, ST_ECFL = 2 };
+enum : int { ST_EINVAL = 1, ST_ECFL = 2, ST_EBOUNDS = 8 };
+
+// Checked builds (-DFWI_CHECKED, the debug build): every global load and store of the time-step
+// kernels first tests its offset against the size of its field; a failing test sets
+// ST_EBOUNDS in the operation's status word and the access is skipped (nothing traps), and
+// fwi_status() reports it.  In the default build the tests compile away.
+#ifdef FWI_CHECKED
+__device__ __forceinline__ bool in_field(long long off, long long len, long long lim, int *status)
+{
+    if (off >= 0 && off + len <= lim) return true;
+    if (status) atomicOr(status, ST_EBOUNDS);
+    return false;
+}
+#define FWI_IN(valid, off, len, lim, status) ((valid) && ::fwi::in_field((off), (len), (lim), (status)))
+#else
+#define FWI_IN(valid, off, len, lim, status) (valid)
+#endif
 
 __device__ __forceinline__ long long cell(const Dims &d, int i, int j) { return (long long)j * d.Px + i; }
 
@@ -198,6 +214,7 @@ __global__ void k_receiver_chain(const long long *__restrict__ idx, int n4, int 
 
 struct Model {
     const float *K, *bx, *bz, *ax, *axh, *az, *azh;
+    int *status;            // the operation's status word (checked builds record out-of-range accesses)
 };
 
 struct Source {
@@ -222,7 +239,8 @@ __global__ void k_sample(const float *__restrict__ p, int ns, int nr, int nt, in
     const float *ps = p + (long long)s * Np;
     float v = 0.f;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v += rw[4 * r + c] * ps[ridx[4 * r + c]];
+    for (int c = 0; c < 4; ++c)
+        if (FWI_IN(true, ridx[4 * r + c], 1, Np, nullptr)) v += rw[4 * r + c] * ps[ridx[4 * r + c]];
     traces[(long long)t * nt + n] = v;
 }
 

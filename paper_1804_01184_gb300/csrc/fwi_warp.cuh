@@ -183,7 +183,8 @@ __device__ __forceinline__ void sample_tail(const Tail &tl, int t)
     const float *ps = tl.field + (long long)s * tl.Np;
     float v = 0.f;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v += tl.rw[4 * r + c] * ps[tl.ridx[4 * r + c]];
+    for (int c = 0; c < 4; ++c)
+        if (FWI_IN(true, tl.ridx[4 * r + c], 1, tl.Np, nullptr)) v += tl.rw[4 * r + c] * ps[tl.ridx[4 * r + c]];
     tl.traces[(long long)t * tl.nt + tl.col] = v;
 }
 
@@ -244,16 +245,20 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         float *pr = ring[ps];
         float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
-        cp16(pr + L.mo, P0, of + L.mc, vf && L.in);
-        if (!L.own) cp16(pr + L.eo, P0, of + L.ec, vf && L.ein);
-        cp16(sg[0] + L.mo, VZ0, orr + L.mc, vr && L.in && L.own);
-        cp16(sg[1] + L.mo, mo.bz, orr + L.mc, vr && L.in && L.own);
-        cp16(sg[2] + L.mo, VX0, oj + L.mc, vj && L.in);
-        cp16(sg[3] + L.mo, mo.bx, oj + L.mc, vj && L.in);
-        cp16(sg[4] + L.mo, mo.K, oj + L.mc, vj && L.in && L.own);
+        const long long np = d.Np;
+        int *stt = mo.status;
+        cp16(pr + L.mo, P0, of + L.mc, FWI_IN(vf && L.in, of + L.mc, 4, np, stt));
+        if (!L.own) cp16(pr + L.eo, P0, of + L.ec, FWI_IN(vf && L.ein, of + L.ec, 4, np, stt));
+        const bool zo = FWI_IN(vr && L.in && L.own, orr + L.mc, 4, np, stt);
+        cp16(sg[0] + L.mo, VZ0, orr + L.mc, zo);
+        cp16(sg[1] + L.mo, mo.bz, orr + L.mc, zo);
+        const bool xo = FWI_IN(vj && L.in, oj + L.mc, 4, np, stt);
+        cp16(sg[2] + L.mo, VX0, oj + L.mc, xo);
+        cp16(sg[3] + L.mo, mo.bx, oj + L.mc, xo);
+        cp16(sg[4] + L.mo, mo.K, oj + L.mc, xo && L.own);
         if (lane == 0) {
-            cp4(&sh.scl[ss][0], mo.az, j, vj);
-            cp4(&sh.scl[ss][1], mo.azh, r, vr);
+            cp4(&sh.scl[ss][0], mo.az, j, FWI_IN(vj, j, 1, d.Nz, stt));
+            cp4(&sh.scl[ss][1], mo.azh, r, FWI_IN(vr, r, 1, d.Nz, stt));
         }
         cp_commit();
     };
@@ -286,7 +291,8 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         for (int k = 1; k <= M; ++k)
             gz = ptap(st.nc[k - 1], pq[M - 1 + k], pq[M - k], gz);
         const float4 vz = pmul(pmul(azh, axv), pfma(ld4(sg[1] + L.mo), gz, ld4(sg[0] + L.mo)));
-        if (L.wr && r >= z0 && r < zend) st4(VZ1 + r * d.Px + L.mc, vz);
+        if (FWI_IN(L.wr && r >= z0 && r < zend, (long long)r * d.Px + L.mc, 4, d.Np, mo.status))
+            st4(VZ1 + r * d.Px + L.mc, vz);
 #pragma unroll
         for (int q = 0; q < R - 1; ++q) vq[q] = vq[q + 1];
         vq[R - 1] = vz;
@@ -298,9 +304,10 @@ __device__ __forceinline__ void fwd_body(const FwdArgs &a, const Strip &sp, FwdS
         const float4 vx = pmul(pmul(az, axhv), pfma(ld4(sg[3] + L.mo), gx, ld4(sg[2] + L.mo)));
         float *vrow = vxr[f & 1];
         st4(vrow + L.mo, vx);
-        if (row && L.wr) st4(VX1 + j * d.Px + L.mc, vx);
+        const bool jw = FWI_IN(row && L.wr, (long long)j * d.Px + L.mc, 4, d.Np, mo.status);
+        if (jw) st4(VX1 + j * d.Px + L.mc, vx);
         __syncwarp();
-        if (row && L.wr) {
+        if (jw) {
             float4 dv = row_dminus<M>(vrow, L.mo, vx, st.nc);          // -dt D-x vx
 #pragma unroll
             for (int k = 1; k <= M; ++k)   // vq[q] is vz row j - M + q
@@ -391,7 +398,8 @@ __device__ __forceinline__ void small_work(const SmallTable &s, int u)
         const float *ps = d.p + (long long)sh * d.Np;
         float v = 0.f;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v += d.rw[4 * r + c] * ps[d.ridx[4 * r + c]];
+        for (int c = 0; c < 4; ++c)
+            if (FWI_IN(true, d.ridx[4 * r + c], 1, d.Np, nullptr)) v += d.rw[4 * r + c] * ps[d.ridx[4 * r + c]];
         d.traces[(long long)l * d.nt + d.n] = v;
         return;
     }
@@ -491,24 +499,30 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
         float *prow = pr[ps];
         float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
+        const long long np = d.Np;
+        int *stt = mo.status;
         if (lane == 0) {
-            cp4(&sh.scl[ss][0], mo.az, f, vf);
-            cp4(&sh.scl[ss][1], mo.azh, r, vr);
-            cp4(&sh.scl[ss][2], mo.az, j, vj);
+            cp4(&sh.scl[ss][0], mo.az, f, FWI_IN(vf, f, 1, d.Nz, stt));
+            cp4(&sh.scl[ss][1], mo.azh, r, FWI_IN(vr, r, 1, d.Nz, stt));
+            cp4(&sh.scl[ss][2], mo.az, j, FWI_IN(vj, j, 1, d.Nz, stt));
         }
-        cp16(prow + L.mo, PN, of + L.mc, vp && L.in);
-        cp16(sg[0] + L.mo, A0, of + L.mc, vf && L.in);
-        cp16(sg[1] + L.mo, mo.K, of + L.mc, vf && L.in);
+        const bool fm = FWI_IN(vf && L.in, of + L.mc, 4, np, stt);
+        cp16(prow + L.mo, PN, of + L.mc, vp && fm);
+        cp16(sg[0] + L.mo, A0, of + L.mc, fm);
+        cp16(sg[1] + L.mo, mo.K, of + L.mc, fm);
         if (!L.own) {
-            cp16(prow + L.eo, PN, of + L.ec, vp && L.ein);
-            cp16(sg[0] + L.eo, A0, of + L.ec, vf && L.ein);
-            cp16(sg[1] + L.eo, mo.K, of + L.ec, vf && L.ein);
+            const bool fe = FWI_IN(vf && L.ein, of + L.ec, 4, np, stt);
+            cp16(prow + L.eo, PN, of + L.ec, vp && fe);
+            cp16(sg[0] + L.eo, A0, of + L.ec, fe);
+            cp16(sg[1] + L.eo, mo.K, of + L.ec, fe);
         }
-        cp16(sg[2] + L.mo, AZ0, orr + L.mc, vr && L.in && L.own);
-        cp16(sg[3] + L.mo, mo.bz, orr + L.mc, vr && L.in && L.own);
-        cp16(sg[4] + L.mo, AX0, oj + L.mc, vj && L.in);
-        cp16(sg[5] + L.mo, mo.bx, oj + L.mc, vj && L.in);
-        cp16(sg[6] + L.mo, A0, oj + L.mc, vj && L.in && L.own);
+        const bool zo = FWI_IN(vr && L.in && L.own, orr + L.mc, 4, np, stt);
+        cp16(sg[2] + L.mo, AZ0, orr + L.mc, zo);
+        cp16(sg[3] + L.mo, mo.bz, orr + L.mc, zo);
+        const bool xo = FWI_IN(vj && L.in, oj + L.mc, 4, np, stt);
+        cp16(sg[4] + L.mo, AX0, oj + L.mc, xo);
+        cp16(sg[5] + L.mo, mo.bx, oj + L.mc, xo);
+        cp16(sg[6] + L.mo, A0, oj + L.mc, xo && L.own);
         cp_commit();
     };
     // qq: K d_p pbar rows f-2M+1 .. f (z-stencil of u_z); bq: bz u_z rows r-2M+1 .. r (z-stencil of
@@ -555,7 +569,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
 #pragma unroll
         for (int q = 0; q < R - 1; ++q) bq[q] = bq[q + 1];
         bq[R - 1] = pmul(ld4(sg[3] + L.mo), uz);
-        if (L.wr && r >= z0 && r < zend) {
+        if (FWI_IN(L.wr && r >= z0 && r < zend, (long long)r * d.Px + L.mc, 4, d.Np, mo.status)) {
             st4(AZ1 + r * d.Px + L.mc, uz);
             red_add4(GZ + r * d.Px + L.mc, pmul(uz, gp));
         }
@@ -567,12 +581,13 @@ __device__ __forceinline__ void adj_body(const AdjArgs &a, const Strip &sp, AdjS
         float *brow = bur[f & 1];
         const float4 bux = pmul(ld4(sg[5] + L.mo), ux);
         st4(brow + L.mo, bux);
-        if (row && L.wr) {
+        const bool jw = FWI_IN(row && L.wr, (long long)j * d.Px + L.mc, 4, d.Np, mo.status);
+        if (jw) {
             st4(AX1 + j * d.Px + L.mc, ux);
             red_add4(GX + j * d.Px + L.mc, pmul(ux, row_dplus<M>(pj, L.mo, pq[0], st.c)));
         }
         __syncwarp();
-        if (row && L.wr) {
+        if (jw) {
             float4 dv = row_dminus<M>(brow, L.mo, bux, st.c);
 #pragma unroll
             for (int k = 1; k <= M; ++k)   // bq[q] is row j - M + q
@@ -631,6 +646,7 @@ __device__ __forceinline__ void inject_entry(float *__restrict__ ap, float *__re
     const float *rs = res + (long long)s * nr * nt + n;
     float a = rw[k] * rs[(long long)(k >> 2) * nt];
     for (m &= CHAIN_FIRST - 1; m < n4; m = rl[m] & (CHAIN_FIRST - 1)) a += rw[m] * rs[(long long)(m >> 2) * nt];
+    if (!FWI_IN(true, ridx[k], 1, Np, nullptr)) return;
     const long long o = (long long)s * Np + ridx[k];
     ap[o] += a;
     accK[o] += a * pn1[o];
@@ -711,15 +727,19 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         float(*sg)[WROW] = stg[ss];
         const int of = f * d.Px, orr = r * d.Px, oj = j * d.Px;
         if (lane == 0) {
-            cp4(&sh.scl[ss][0], mo.az, j, vj);
-            cp4(&sh.scl[ss][1], mo.azh, r, vr);
+            cp4(&sh.scl[ss][0], mo.az, j, FWI_IN(vj, j, 1, d.Nz, mo.status));
+            cp4(&sh.scl[ss][1], mo.azh, r, FWI_IN(vr, r, 1, d.Nz, mo.status));
         }
-        const bool zo = vr && L.in && L.own, xo = vj && L.in;
-        cp16(pr + L.mo, P0, of + L.mc, vf && L.in);
-        cp16(qr + L.mo, Q0, of + L.mc, vf && L.in);
+        const long long np = d.Np;
+        int *stt = mo.status;
+        const bool zo = FWI_IN(vr && L.in && L.own, orr + L.mc, 4, np, stt),
+                   xo = FWI_IN(vj && L.in, oj + L.mc, 4, np, stt), fm = FWI_IN(vf && L.in, of + L.mc, 4, np, stt);
+        cp16(pr + L.mo, P0, of + L.mc, fm);
+        cp16(qr + L.mo, Q0, of + L.mc, fm);
         if (!L.own) {
-            cp16(pr + L.eo, P0, of + L.ec, vf && L.ein);
-            cp16(qr + L.eo, Q0, of + L.ec, vf && L.ein);
+            const bool fe = FWI_IN(vf && L.ein, of + L.ec, 4, np, stt);
+            cp16(pr + L.eo, P0, of + L.ec, fe);
+            cp16(qr + L.eo, Q0, of + L.ec, fe);
         }
         cp16(sg[0] + L.mo, VZ0, orr + L.mc, zo);
         cp16(sg[1] + L.mo, UZ0, orr + L.mc, zo);
@@ -765,7 +785,7 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         const float4 fz = pmul(azh, axv), bz = ld4(sg[2] + L.mo);
         const float4 vz = pmul(fz, pfma(bz, gp, ld4(sg[0] + L.mo)));
         const float4 uz = pmul(fz, pfma(ld4(sg[3] + L.mo), gp, pfma(bz, gq, ld4(sg[1] + L.mo))));
-        if (L.wr && r >= z0 && r < zend) {
+        if (FWI_IN(L.wr && r >= z0 && r < zend, (long long)r * d.Px + L.mc, 4, d.Np, mo.status)) {
             st4(VZ1 + r * d.Px + L.mc, vz);
             st4(UZ1 + r * d.Px + L.mc, uz);
         }
@@ -784,12 +804,13 @@ __device__ __forceinline__ void born_body(const BornArgs &a, const Strip &sp, Bo
         float *vrow = svr[f & 1], *urow = sur[f & 1];
         st4(vrow + L.mo, vx);
         st4(urow + L.mo, ux);
-        if (row && L.wr) {
+        const bool jw = FWI_IN(row && L.wr, (long long)j * d.Px + L.mc, 4, d.Np, mo.status);
+        if (jw) {
             st4(VX1 + j * d.Px + L.mc, vx);
             st4(UX1 + j * d.Px + L.mc, ux);
         }
         __syncwarp();
-        if (row && L.wr) {
+        if (jw) {
             float4 dv = row_dminus<M>(vrow, L.mo, vx, st.nc), du = row_dminus<M>(urow, L.mo, ux, st.nc);
 #pragma unroll
             for (int k = 1; k <= M; ++k) {   // vq[q] is vz row j - M + q

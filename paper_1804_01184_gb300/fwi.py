@@ -12,6 +12,7 @@ or no CUDA device is present, these functions raise.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import threading
@@ -59,6 +60,35 @@ _lib = None
 _lock = threading.Lock()
 
 
+def _open(path):
+    """Loads the library at `path` and binds every single-job entry point."""
+    L = C.CDLL(path)
+    gp, vp, dp = C.POINTER(Grid), C.c_void_p, C.c_void_p
+    sp, rp = C.POINTER(_Sources), C.POINTER(_Receivers)
+    L.fwi_workspace_bytes.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_size_t]
+    L.fwi_workspace_bytes.restype = C.c_size_t
+    L.fwi_model.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp, C.c_size_t, vp]
+    L.fwi_born.argtypes = [gp, C.c_int, vp, vp, vp, vp, sp, rp, vp, vp, C.c_size_t, vp]
+    L.fwi_adjoint.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, vp, C.c_size_t, vp]
+    L.fwi_gradient.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, dp, vp, C.c_size_t, vp]
+    L.fwi_status.argtypes = [vp, vp]
+    L.fwi_misfit.argtypes = [vp, vp, C.c_longlong, vp, vp]
+    L.fwi_misfit_weighted.argtypes = [vp, vp, C.c_longlong, C.c_int, vp, vp, vp]
+    L.fwi_gradient_weighted.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp, dp, dp, vp, C.c_size_t, vp]
+    L.fwi_last_error.restype = C.c_char_p
+    L.fwi_launch_count.restype = C.c_longlong
+    L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
+    L.fwi_set_checkpoint.argtypes = [C.c_int]
+    L.fwi_set_accumulation.argtypes = [C.c_int]
+    L.fwi_trace.argtypes = [C.c_int]
+    L.fwi_trace_report.argtypes = [C.c_char_p, C.c_size_t]
+    L.fwi_model_noalloc.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp]
+    L.fwi_status_noalloc.argtypes = [vp]
+    L.fwi_profile.argtypes = [C.c_int]
+    L.fwi_profile_report.argtypes = [C.c_char_p, C.c_size_t]
+    return L
+
+
 def lib():
     """The loaded libfwi.so (raises if it has not been built)."""
     global _lib
@@ -67,32 +97,25 @@ def lib():
             path = _build.LIB
             if not os.path.exists(path):
                 raise RuntimeError(f"libfwi.so is not built ({path}); run paper_1804_01184_gb300.build.build()")
-            L = C.CDLL(path)
-            gp, vp, dp = C.POINTER(Grid), C.c_void_p, C.c_void_p
-            sp, rp = C.POINTER(_Sources), C.POINTER(_Receivers)
-            L.fwi_workspace_bytes.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_size_t]
-            L.fwi_workspace_bytes.restype = C.c_size_t
-            L.fwi_model.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp, C.c_size_t, vp]
-            L.fwi_born.argtypes = [gp, C.c_int, vp, vp, vp, vp, sp, rp, vp, vp, C.c_size_t, vp]
-            L.fwi_adjoint.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, vp, C.c_size_t, vp]
-            L.fwi_gradient.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, dp, dp, vp, C.c_size_t, vp]
-            L.fwi_status.argtypes = [vp, vp]
-            L.fwi_misfit.argtypes = [vp, vp, C.c_longlong, vp, vp]
-            L.fwi_misfit_weighted.argtypes = [vp, vp, C.c_longlong, C.c_int, vp, vp, vp]
-            L.fwi_gradient_weighted.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp, dp, dp, vp, C.c_size_t, vp]
-            L.fwi_last_error.restype = C.c_char_p
-            L.fwi_launch_count.restype = C.c_longlong
-            L.fwi_set_tile.argtypes = [C.c_int, C.c_int]
-            L.fwi_set_checkpoint.argtypes = [C.c_int]
-            L.fwi_set_accumulation.argtypes = [C.c_int]
-            L.fwi_trace.argtypes = [C.c_int]
-            L.fwi_trace_report.argtypes = [C.c_char_p, C.c_size_t]
-            L.fwi_model_noalloc.argtypes = [gp, C.c_int, vp, vp, sp, rp, vp, vp]
-            L.fwi_status_noalloc.argtypes = [vp]
-            L.fwi_profile.argtypes = [C.c_int]
-            L.fwi_profile_report.argtypes = [C.c_char_p, C.c_size_t]
-            _lib = L
+            _lib = _open(path)
     return _lib
+
+
+@contextlib.contextmanager
+def library(path):
+    """Runs the single-job calls made inside the block on the library at `path` -- e.g. the
+    bounds-checked debug build, build.LIB_CHECKED -- then returns to the default one."""
+    global _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built")
+    with _lock:
+        prev = _lib
+        _lib = _open(path)
+    try:
+        yield _lib
+    finally:
+        with _lock:
+            _lib = prev
 
 
 def _raise(rc):
