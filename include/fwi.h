@@ -42,7 +42,7 @@ extern "C" {
 #define FWI_EINVAL   -1   /* bad size, null pointer, 1 + xi <= 0, position off the grid */
 #define FWI_ECFL     -2   /* dt above the stability limit of the stencil for the model */
 #define FWI_ENOMEM   -3   /* workspace smaller than the operation's minimum             */
-#define FWI_ETIMEOUT -4   /* reserved for bounded device-side waits; no call returns it */
+#define FWI_ETIMEOUT -4   /* a bounded device-side wait expired (fwi_fborn_status) */
 #define FWI_ECUDA    -5   /* a CUDA runtime call failed                                 */
 
 /* Parameterizations of Table 1; contrasts xi = (m - m_o)/m_o of the named pair. */
@@ -394,6 +394,12 @@ int fwi_fborn_misfit(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param p
  * eqn:param_Hker.  FWI_EINVAL for a node off the grid or more than 2048 sources + receivers. */
 int fwi_fborn_hessian(const fwi_fgrid *g, int ns, int nr, fwi_param pz, int jx, int jz, void *work, double *H,
                       void *stream);
+
+/* Device-side status of the acquisition's workspace since the last call of this function
+ * (synchronizes `stream`, then clears it): FWI_ETIMEOUT if a bounded wait inside the tensor-core
+ * data contraction of fwi_fborn_model / _gradient / _misfit expired (its results are then
+ * invalid; the kernel still released its tensor memory), else FWI_OK. */
+int fwi_fborn_status(const fwi_fgrid *g, int ns, int nr, void *work, void *stream);
 
 #ifdef __cplusplus
 }

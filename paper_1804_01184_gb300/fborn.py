@@ -44,6 +44,7 @@ def lib():
         L.fwi_fborn_gradient.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.fwi_fborn_hessian.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
         L.fwi_fborn_misfit.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+        L.fwi_fborn_status.argtypes = [gp, C.c_int, C.c_int, vp, vp]
         _bound = True
     return L
 
@@ -130,6 +131,11 @@ class Acquisition:
         F._raise(lib().fwi_fborn_hessian(C.byref(self.fg), self.ns, self.nr, int(pz), int(jx), int(jz),
                                          F._ptr(self.work), F._ptr(out), F._stream(stream)))
         return out
+
+    def status(self, stream=None):
+        """Raises FwiError(FWI_ETIMEOUT) if a bounded device-side wait of the data contraction
+        expired since the last check (fwi_fborn_status); synchronizes the stream."""
+        F._raise(lib().fwi_fborn_status(C.byref(self.fg), self.ns, self.nr, F._ptr(self.work), F._stream(stream)))
 
     def reduced_hessian(self, pz, jx, jz, stream=None):
         return self.hessian(pz, jx, jz, stream=stream)[:, :, jz, jx]

@@ -69,7 +69,8 @@ def test_fborn_workspace_planning(L):
     tables = 2 * 60 * 110 * rows * 8
     chunks = (121 * 121 + 255) // 256
     freq_partials = 60 * 4 * 121 * 121 * 8
-    assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + freq_partials + (1 << 16)
+    contrasts = 2 * rows * 4                   # FP32 contrasts of the data contraction
+    assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + freq_partials + contrasts + (1 << 16)
     with pytest.raises(fwi.FwiError):
         fborn.fwi_fborn_workspace_bytes(fborn.make_fgrid(121, 121, 0, 5.0, 0.0, 0.0), 10, 100)
     with pytest.raises(fwi.FwiError):

@@ -146,6 +146,7 @@ def test_deterministic_and_errors(B):
     _, g1 = acq.gradient(2, w.xi_a, w.xi_b, d1 * 0.9)
     _, g2 = acq.gradient(2, w.xi_a, w.xi_b, d1 * 0.9)
     np.testing.assert_array_equal(g1.cpu().numpy(), g2.cpu().numpy())
+    acq.status()                                          # no bounded wait of the contraction expired
     fg = B.make_fgrid(w.nx, w.nz, w.nf, w.dx, w.x0, w.z0)
     on_node = w.src_xy.copy()
     on_node[0] = (w.x0 + 2 * w.dx, w.z0 + 3 * w.dx)
