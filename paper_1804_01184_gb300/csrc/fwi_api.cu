@@ -1,7 +1,9 @@
 // fwi_api.cu -- host side of libfwi.so: argument checks, workspace plans, time loops.
 // The C ABI is declared in include/fwi.h.  Every arithmetic step of the method runs in the
 // kernels of fwi_kernels.cuh; this file only plans memory and orders launches.
+#include <cuda.h>          // CUtensorMap and its enums (the encoder is looked up at run time)
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>

@@ -208,6 +208,26 @@ def test_degenerate_cases(B):
     assert rel_l2(H, refH) <= HESS_TOL
 
 
+@pytest.mark.parametrize("rho_o, vp_o, amp", [(1.0, 1500.0, 0.15), (2.5e6, 4000.0, 0.15), (2000.0, 2000.0, 1e-6),
+                                           (2000.0, 2000.0, 0.9)])
+def test_row_scaling_over_magnitudes(B, rho_o, vp_o, amp):
+    """The tensor-core data contraction scales each operand row by a power of two taken from
+    the tables' and the contrasts' largest values before its FP16 split: Born data for
+    reference media and contrast amplitudes spanning many decades (table values from ~0.1 to
+    ~1e6, contrasts from 1e-6 to ~1e3 under the exact map) match the oracle to the same
+    tolerance, and no bounded wait expires."""
+    import dataclasses
+    w = dataclasses.replace(I.small_freq_case(seed=21, nx=17, nz=13, ns=5, nr=40, nf=3, amp=amp), rho_o=rho_o,
+                            vp_o=vp_o)
+    acq = B.acquisition(w)
+    for scheme in (1, 2):
+        d = acq.model(0, w.xi_a, w.xi_b, scheme=scheme, incident=False).cpu().numpy()
+        ref = oracle_data(w, 0, w.xi_a, w.xi_b, scheme, incident=False)
+        assert np.isfinite(d).all()
+        assert crel(d, ref) <= TRACE_TOL
+    acq.status()
+
+
 def test_diffraction_patterns(B):
     """Sec. "Diffraction-pattern Analysis": a unit point contrast at x_0 with sources and
     receivers on a circle around it scatters the same energy at every angle for 1/K (and K, and
