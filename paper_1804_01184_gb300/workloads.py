@@ -512,6 +512,19 @@ FB_FLOPS_PER_TERM = 24      # three complex multiply-adds per (frequency, source
 FP32_LANES_PER_SM = 128
 
 
+def measured_hbm_gbs():
+    """(HBM copy bandwidth in GB/s, its source): MEASURED_PEAKS.json's hbm_gbs at the repository
+    root, else the machine's fallback figure."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        if "hbm_gbs" in pk:
+            return float(pk["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback"
+
+
 def fp32_peak_tflops(sm_mhz):
     """FP32 FMA peak of the GPU at the given SM clock: SMs x 128 lanes x 2 flops x clock."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -580,14 +593,54 @@ def bench_fborn(args, Clocks, cpu_sample=None):
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = 5 * (2 * w.nx * w.nz * 4 + q_host.nbytes)
     d2h = 5 * (8 + 2 * w.nx * w.nz * 8 + 4 * w.nx * w.nz * 8)
-    # dominant kernel: the roofline of the FP32 pipe (bound "alu")
+    # rooflines: the tensor-core data contraction is bound by streaming the tables from HBM
+    # (every table value of every point read once, plus the chunk partials written); the
+    # gradient and the Hessian column by the FP32 pipe (24 algorithmic flops per term)
     kern = prof["kernels"]
-    name = max(kern, key=lambda k: kern[k]["ms"])
-    per_launch_ms = kern[name]["ms"] / kern[name]["launches"]
-    flops = FB_FLOPS_PER_TERM * terms
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(sm_mhz)
-    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    fp32_peak = fp32_peak_tflops(sm_mhz)
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    P, N = w.src_xy.shape[0] + w.rec_xy.shape[0], w.nx * w.nz
+    nchunk = (N + 255) // 256
+    table_bytes = 16 * w.nf * P * N + 8 * nchunk * w.nf * w.src_xy.shape[0] * w.rec_xy.shape[0]
+    flops = FB_FLOPS_PER_TERM * terms
+
+    def traffic(k):
+        """DRAM bytes per launch from the committed ncu capture (profiles/traffic_fborn.json);
+        None when the kernels changed since it was taken."""
+        import hashlib
+        import json
+        import os
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        path = os.path.join(root, "profiles", "traffic_fborn.json")
+        if not os.path.exists(path):
+            return None
+        t = json.load(open(path))
+        src = open(os.path.join(root, "paper_1804_01184_gb300", "csrc", "fwi_fborn.inc"), "rb").read()
+        short = k.split("::")[-1].split("<")[0]
+        if t.get("kernel_source_sha256") != hashlib.sha256(src).hexdigest() or short not in t.get("kernels", {}):
+            return None
+        return t["kernels"][short]["dram_bytes_per_launch"]
+
+    def roof(k):
+        per_launch_ms = kern[k]["ms"] / kern[k]["launches"]
+        if "model_tc" in k:
+            a = table_bytes / (per_launch_ms / 1e3) / 1e9
+            return {"kernel": k, "bound": "hbm", "achieved": round(a, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(a / hbm_peak, 4), "traffic": traffic(k), "bytes_per_launch": table_bytes,
+                    "avg_launch_us": round(1e3 * per_launch_ms, 2), "peak_source": hbm_src}
+        # the Hessian column's Gram sums: 9 complex multiply-adds (72 flops) per (frequency, point, node)
+        fl = 72 * w.nf * P * N if "hess" in k else flops
+        a = fl / (per_launch_ms / 1e3) / 1e12
+        return {"kernel": k, "bound": "alu", "achieved": round(a, 2), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(a / fp32_peak, 4), "traffic": traffic(k), "flops_per_launch": fl,
+                "avg_launch_us": round(1e3 * per_launch_ms, 2),
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 flops x max SM clock"}
+
+    name = max(kern, key=lambda k: kern[k]["ms"])
+    roofline = roof(name)
+    rooflines = {k: roof(k) for k in kern if any(t in k for t in ("model_tc", "k_fb_grad<", "k_fb_hess"))
+                 and "sum" not in k}
     cpu = cpu_sample(w) if (cpu_sample and not args.no_cpu) else None
     # diffraction patterns (Sec. "Diffraction-pattern Analysis"): energy scattered by a unit
     # point contrast of each parameter at x_0, relative to its maximum, by scattering angle
@@ -619,10 +672,7 @@ def bench_fborn(args, Clocks, cpu_sample=None):
                    "acquisition": "10 sources, 100 receivers, 490 m circle", "frequencies": "60 (0.25-15 Hz)",
                    "step": "5 x (Scheme I gradient + Hessian column at x_0)",
                    "l2": "Green tables 1.55 GB, larger than L2", "tables_ms": round(tables_ms, 1)},
-        "roofline": {"kernel": name, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
-                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                     "flops_per_launch": flops, "avg_launch_us": round(1e3 * per_launch_ms, 2),
-                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 flops x max SM clock"},
+        "roofline": roofline, "kernel_rooflines": rooflines,
         "kernels": kern, "gpu_launches": sum(v["launches"] for v in kern.values()) // max(args.steps, 1),
         "clocks": clk,
         "e2e": {"value": round(passes * terms / e2e_s / 1e9, 3), "unit": "GW-terms/s", "h2d_bytes_per_step": h2d,
