@@ -382,6 +382,15 @@ int fwi_fborn_gradient(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param
                        const float *xi_b, const float *data_obs, void *work, double *misfit, double *grad,
                        void *stream);
 
+/* fwi_fborn_gradient and fwi_fborn_hessian(pz, jx, jz) in one call: misfit, gradient [2][nz][nx]
+ * and the Scheme I Hessian terms H [2][2][nz][nx] of node (jx, jz), both as the two calls give
+ * them, with the Hessian's sums formed in the gradient's pass over the Green tables (one table
+ * pass instead of two).  FWI_EINVAL for bad arguments, a node off the grid or more than 2048
+ * sources + receivers. */
+int fwi_fborn_gradient_hessian(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param pz, const float *xi_a,
+                               const float *xi_b, const float *data_obs, int jx, int jz, void *work, double *misfit,
+                               double *grad, double *H, void *stream);
+
 /* The misfit J alone (one double), as fwi_fborn_gradient computes it: the data contraction,
  * the residual and the reduction, without the gradient pass (line searches). */
 int fwi_fborn_misfit(const fwi_fgrid *g, int ns, int nr, int scheme, fwi_param pz, const float *xi_a,

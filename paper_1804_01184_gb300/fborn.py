@@ -45,6 +45,8 @@ def lib():
         L.fwi_fborn_hessian.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
         L.fwi_fborn_misfit.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
         L.fwi_fborn_status.argtypes = [gp, C.c_int, C.c_int, vp, vp]
+        L.fwi_fborn_gradient_hessian.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int, C.c_int,
+                                                 vp, vp, vp, vp, vp]
         _bound = True
     return L
 
@@ -113,6 +115,22 @@ class Acquisition:
                                           F._ptr(xb), F._ptr(q), F._ptr(self.work), F._ptr(misfit), F._ptr(grad),
                                           F._stream(stream)))
         return misfit, grad
+
+    def gradient_hessian(self, pz, xi_a, xi_b, data_obs, jx, jz, scheme=LINEAR, misfit=None, grad=None, H=None,
+                         stream=None):
+        """(misfit [1], gradient [2][nz][nx], Hessian terms [2][2][nz][nx] of node (jx, jz)), all
+        float64, from one pass over the tables (fwi_fborn_gradient_hessian)."""
+        xa, xb, q = F._dev(xi_a), F._dev(xi_b), _complex_dev(data_obs)
+        if misfit is None:
+            misfit = torch.empty(1, dtype=torch.float64, device="cuda")
+        if grad is None:
+            grad = torch.empty((2,) + self.shape, dtype=torch.float64, device="cuda")
+        if H is None:
+            H = torch.empty((2, 2) + self.shape, dtype=torch.float64, device="cuda")
+        F._raise(lib().fwi_fborn_gradient_hessian(C.byref(self.fg), self.ns, self.nr, int(scheme), int(pz), F._ptr(xa),
+                                                  F._ptr(xb), F._ptr(q), int(jx), int(jz), F._ptr(self.work),
+                                                  F._ptr(misfit), F._ptr(grad), F._ptr(H), F._stream(stream)))
+        return misfit, grad, H
 
     def misfit(self, pz, xi_a, xi_b, data_obs, scheme=LINEAR, out=None, stream=None):
         """Misfit [1] float64 alone (fwi_fborn_misfit)."""

@@ -68,7 +68,7 @@ def test_fborn_workspace_planning(L):
     rows = (121 * 121 + 127) // 128 * 128      # table rows padded to 128 nodes
     tables = 2 * 60 * 110 * rows * 8
     chunks = (121 * 121 + 255) // 256
-    freq_partials = 60 * 4 * 121 * 121 * 8
+    freq_partials = 60 * 6 * 121 * 121 * 8      # gradient [nf][2][N], Hessian [nf][4][N]
     contrasts = 2 * rows * 4                   # FP32 contrasts of the data contraction
     assert tables <= n <= tables + (chunks + 3) * 60 * 10 * 100 * 8 + freq_partials + contrasts + (1 << 16)
     with pytest.raises(fwi.FwiError):

@@ -87,6 +87,27 @@ def test_hessian_column_matches_oracle(B, case, pz):
             assert rel_l2(H[a, b], ref[a, b]) <= 10 * HESS_TOL
 
 
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_gradient_hessian_in_one_pass(B, case, scheme):
+    """fwi_fborn_gradient_hessian gives what fwi_fborn_gradient and fwi_fborn_hessian give
+    separately (the same sums in the same order, bitwise), and its Hessian matches the oracle;
+    with 17 sources (two source blocks) and 130 receivers (two residual tiles)."""
+    w = I.small_freq_case(**case)
+    acq = B.acquisition(w)
+    a0, b0 = 0.5 * w.xi_a, -0.3 * w.xi_b
+    q = acq.model(1, w.xi_a, w.xi_b, scheme=2).cpu().numpy()
+    jx, jz = w.nx // 3, w.nz // 2
+    for pz in (0, 2, 4):
+        J, G = acq.gradient(pz, a0, b0, q, scheme=scheme)
+        H = acq.hessian(pz, jx, jz)
+        J2, G2, H2 = acq.gradient_hessian(pz, a0, b0, q, jx, jz, scheme=scheme)
+        assert torch.equal(J, J2) and torch.equal(G, G2) and torch.equal(H, H2)
+    ref = FB.hessian_column(ofg(w), w.freqs, w.spectrum, w.src_xy, w.rec_xy, 4, jz * w.nx + jx)
+    assert rel_l2(H2.cpu().numpy(), ref) <= HESS_TOL
+    acq.status()
+
+
 def test_reduced_hessian_cross_terms_paper_claim(B):
     """With sources and receivers evenly around x_0 the K-rho and 1/K-1/rho reduced Hessians
     have no cross-parameter term (to FP32 rounding); vp-rho, Ip-rho and vp-Ip do."""
