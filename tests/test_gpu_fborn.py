@@ -181,6 +181,16 @@ def test_deterministic_and_errors(B):
         acq.hessian(0, w.nx, 0)
     with pytest.raises(F.FwiError):
         acq.model(0, w.xi_a, w.xi_b, scheme=3)
+    with pytest.raises(F.FwiError):
+        acq.gradient_hessian(0, w.xi_a, w.xi_b, d1, w.nx, 0)           # node off the grid
+    # the Hessian terms keep u_p(x_j) of every point in shared memory: at most 2048 points
+    big = I.small_freq_case(seed=8, nx=3, nz=3, ns=1000, nr=1049, nf=1)
+    ab = B.acquisition(big)
+    qb = np.zeros((1, big.ns, big.nr), np.complex64)
+    for call in (lambda: ab.hessian(0, 1, 1), lambda: ab.gradient_hessian(0, big.xi_a, big.xi_b, qb, 1, 1)):
+        with pytest.raises(F.FwiError):
+            call()
+    acq.status()
 
 
 def test_born_inversions_converge(B):
